@@ -1,0 +1,436 @@
+#!/usr/bin/env python3
+"""Benchmark of the fast zeta and Moebius transforms on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over one synthetic poset function:
+the zeta transform (chain scan + niv gather) of f, then the Moebius transform
+(forward substitution + V^-1) of the result. The value is node-values/s:
+2 * n * B output values per step (n * B from each transform) over the
+device time of the step, summed over K steps (CUDA events on the launching
+stream; the L2 is flushed between steps, outside the timed events).
+
+Default workload: planted-chain poset n = 2^20, k = 64 chains of 16384, cross
+out-degree 3, f fp64 uniform in [-1, 1], B = 1 (plain FP64 GPU form). Extra
+lines ("variants") time the same poset with int64 and FP32-compensated values
+and the antichain-level Moebius schedule.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mz|reference]
+
+For N > 1, launch under torch.distributed.run: every rank runs an independent
+replica (its own poset, seed + rank) with no collective on the data path, and
+the value is the sum over ranks divided by the slowest rank's time.
+--impl reference times the CPU oracle (exact per-row definition) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import posetgen as pg  # noqa: E402
+
+METRIC = "zeta & Möbius node-values/s, % HBM peak; FP32-compensated vs FP64 plain"
+UNIT = "node-values/s"
+
+WORKLOADS = {
+    "c1": dict(n=4096, k=16, cross_p=4 / 4096, desc="planted poset n=4096, k=16 chains of 256, cross edges w.p. 4/n"),
+    "c2": dict(n=1 << 20, k=64, cross_deg=3,
+               desc="planted poset n=2^20, k=64 chains of 16384, cross-chain out-degree 3"),
+    "c3": dict(n=1 << 22, k=128, cross_deg=2,
+               desc="planted poset n=2^22, k=128 chains of 32768, cross-chain out-degree 2"),
+}
+DTYPES = {"f64": ("f64u", "fp64 uniform [-1,1]"), "i64": ("i64:1048576", "int64 uniform [-2^20,2^20]"),
+          "f32c": ("f32u", "fp32 uniform [-1,1] as F32C pairs")}
+
+
+def make_poset(wl: str, seed: int):
+    w = WORKLOADS[wl]
+    kw = {"cross_p": w["cross_p"]} if "cross_p" in w else {"cross_deg": w["cross_deg"]}
+    return pg.planted_chain_poset(w["n"], w["k"], seed, **kw)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("mz_kernels.cu", "mz_arith.cuh"):
+        with open(os.path.join(ROOT, "paper_2211_13706_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str, workload: str, dtype: str):
+    """DRAM bytes per launch from the committed ncu summary, or None if absent/stale."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src_hash = None
+    vals = {}
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("source_hash:"):
+            src_hash = line.split(":", 1)[1].strip()
+        elif line and not line.startswith("#") and "=" in line:
+            key, v = line.split("=", 1)
+            vals[key.strip()] = v.split()[0]
+    if src_hash != kernel_source_hash():
+        return None
+    v = vals.get(f"{kernel}/{workload}/{dtype}")
+    return float(v) if v else None
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- device arm
+def algorithmic_bytes(kernel: str, n: int, k: int, B: int) -> int:
+    """Bytes a launch must move (the design doc lists them): maps, inputs, outputs; the
+    prefix array y' counts only where it is written or read as an input/output."""
+    if kernel == "chain_scan":
+        return 8 * n * B + 4 * (n + k) + 8 * (n + k) * B
+    if kernel == "niv_gather":
+        return 4 * n * k + 4 * n + 8 * n * B
+    if kernel == "mob_init":
+        return 4 * (n + k) + 8 * (n + k) * B
+    if kernel == "mob_wave":
+        return 4 * n * k + 8 * n + 8 * n * B + 8 * n * B
+    if kernel == "mob_diff":
+        return 4 * (n + k) + 8 * (n + k) * B + 8 * n * B
+    raise KeyError(kernel)
+
+
+ZETA_KERNELS = ["chain_scan", "niv_gather"]
+MOB_KERNELS = ["mob_init", "mob_wave", "mob_diff"]
+MOB_KERNELS_ANTI = ["mob_init", "mob_wave"]
+
+
+def to_dev(x, dtype_key, torch):
+    if dtype_key == "f32c":
+        hi = np.asarray(x, dtype=np.float32)
+        return torch.from_numpy(np.stack([hi, np.zeros_like(hi)])).cuda()
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def time_transforms(mz, plan, x, steps, warmup, torch, flush, anti=False, sampler=None):
+    """Runs `warmup` + `steps` steps (zeta then Moebius); returns per-kernel mean ms,
+    total device ms of the timed steps, and the launch count."""
+    stream = torch.cuda.current_stream()
+    nz, nm = len(ZETA_KERNELS), len(MOB_KERNELS_ANTI if anti else MOB_KERNELS)
+    ev_z = [torch.cuda.Event(enable_timing=True) for _ in range(nz + 1)]
+    ev_m = [torch.cuda.Event(enable_timing=True) for _ in range(nm + 1)]
+    for e in ev_z + ev_m:            # create the underlying cudaEvent_t
+        e.record(stream)
+    torch.cuda.synchronize()
+    g = torch.empty_like(x)
+    y = torch.empty_like(x)
+    sums = np.zeros(nz + nm)
+    total = 0.0
+    launches = 0
+    for it in range(warmup + steps):
+        if it == warmup:
+            torch.cuda.synchronize()
+            if sampler:
+                sampler.start()
+        flush.zero_()                 # L2 flush, outside the timed events
+        mz.mz_set_launch_events([e.cuda_event for e in ev_z])
+        plan.zeta(x, out=g)
+        lz = mz.mz_last_launch_count()
+        mz.mz_set_launch_events([e.cuda_event for e in ev_m])
+        plan.mobius(g, out=y)
+        lm = mz.mz_last_launch_count()
+        mz.mz_set_launch_events(None)
+        ev_m[-1].synchronize()
+        if it >= warmup:
+            tz = [ev_z[i].elapsed_time(ev_z[i + 1]) for i in range(nz)]
+            tm = [ev_m[i].elapsed_time(ev_m[i + 1]) for i in range(nm)]
+            sums += np.array(tz + tm)
+            total += ev_z[0].elapsed_time(ev_z[-1]) + ev_m[0].elapsed_time(ev_m[-1])
+            launches += lz + lm
+    clocks = sampler.stop() if sampler else None
+    plan.check()
+    names = ZETA_KERNELS + (MOB_KERNELS_ANTI if anti else MOB_KERNELS)
+    return {n_: s / steps for n_, s in zip(names, sums)}, total, launches, clocks, g, y
+
+
+def time_e2e(mz, plan, f_np, dtype_key, steps, torch):
+    """Same step through the public API from pinned host memory: H2D of f, zeta,
+    Moebius, D2H of both results, all inside the timed events."""
+    x = to_dev(f_np, dtype_key, torch)
+    h_in = x.cpu().pin_memory()
+    h_g = torch.empty_like(h_in).pin_memory()
+    h_f = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(x)
+    d_g = torch.empty_like(x)
+    d_f = torch.empty_like(x)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for it in range(steps + 2):
+        torch.cuda.synchronize()
+        e0.record(st)
+        d_in.copy_(h_in, non_blocking=True)
+        plan.zeta(d_in, out=d_g)
+        plan.mobius(d_g, out=d_f)
+        h_g.copy_(d_g, non_blocking=True)
+        h_f.copy_(d_f, non_blocking=True)
+        e1.record(st)
+        e1.synchronize()
+        if it >= 2:
+            total += e0.elapsed_time(e1)
+    plan.check()
+    nbytes = x.numel() * x.element_size()
+    return total, nbytes, 2 * nbytes
+
+
+def cpu_baseline(p, f_np, budget_s: float, max_rows: int):
+    """The CPU oracle as it stands: exact zeta rows (BFS reachability + exact sum)."""
+    import oracle
+    rng = np.random.default_rng(123)
+    rows = rng.choice(p.n, max_rows, replace=False).tolist()
+    t0 = time.perf_counter()
+    done = 0
+    for r in rows:
+        oracle.zeta_rows(p.n, p.src, p.dst, f_np, [r])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} zeta rows of this poset (exact: BFS reachability + exact sum), single thread; "
+                      "the oracle's Moebius has no per-row form cheaper than O(|out(x)|^2)"}
+
+
+def device_arm(args):
+    import torch
+    import paper_2211_13706_gb300 as mz
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    wl = WORKLOADS[args.workload]
+    p = make_poset(args.workload, 1 + rank)
+    t0 = time.perf_counter()
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id)
+    build_s = time.perf_counter() - t0
+    info = plan.info
+    kind, fdesc = DTYPES[args.dtype]
+    f_np = pg.function_values(p.n, 1, kind, 2 + rank)[:, 0]
+    x = to_dev(f_np, args.dtype, torch)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    kt, total_ms, launches, clocks, g, y = time_transforms(mz, plan, x, args.steps, args.warmup, torch, flush,
+                                                           sampler=sampler)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n, k, B = p.n, info["k"], 1
+    units = 2 * n * B * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # round-trip sanity on the timed data (Moebius(zeta(f)) = f)
+    if args.dtype == "i64":
+        assert torch.equal(y, x), "Moebius(zeta(f)) != f"
+
+    e2e_ms, h2d, d2h = time_e2e(mz, plan, f_np, args.dtype, max(5, min(args.steps, 50)), torch)
+    e2e_steps = max(5, min(args.steps, 50))
+    e2e_val = 2 * n * B * e2e_steps * world / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = load_peaks()
+    dom = max(kt, key=kt.get)
+    alg = algorithmic_bytes(dom, n, k, B)
+    achieved = alg / (kt[dom] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "traffic": load_traffic(dom, args.workload, args.dtype), "algorithmic_bytes": alg,
+            "mean_launch_ms": round(kt[dom], 5)}
+    kernels = {name: {"mean_ms": round(v, 5), "share": round(v / sum(kt.values()), 4),
+                      "alg_GBps": round(algorithmic_bytes(name, n, k, B) / (v / 1e3) / 1e9, 1)}
+               for name, v in kt.items()}
+
+    variants = {}
+    if not args.no_variants:
+        for vd in ("i64", "f32c"):
+            if vd == args.dtype:
+                continue
+            fv = pg.function_values(p.n, 1, DTYPES[vd][0], 3)[:, 0]
+            xv = to_dev(fv, vd, torch)
+            ktv, tot, _, _, _, _ = time_transforms(mz, plan, xv, args.variant_steps, 3, torch, flush)
+            variants[vd] = {"value": 2 * n * args.variant_steps / (tot / 1e3),
+                            "ms_per_step": tot / args.variant_steps,
+                            "kernels_ms": {a: round(b, 5) for a, b in ktv.items()}}
+        pa = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
+        kta, tot, _, _, _, _ = time_transforms(mz, pa, x, 3, 1, torch, flush, anti=True)
+        variants["mobius_antichain_schedule_" + args.dtype] = {
+            "mobius_ms": round(kta["mob_init"] + kta["mob_wave"], 4), "levels": pa.info["levels"],
+            "note": "Alg. 5/6 schedule (antichain levels) instead of U's dependency levels"}
+        pa.close()
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, f_np, args.cpu_budget, 64)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "i64": "int64", "f32c": "f32c"}[args.dtype],
+        "data": "synthetic",
+        "config": {"workload": wl["desc"] + f"; f {fdesc}; B=1", "n": n, "k": k, "batch": B,
+                   "nnz": info["nnz"], "levels": info["levels"], "ulevels": info["ulevels"],
+                   "units": "2*n*B node-values per step (zeta output + Moebius output)",
+                   "l2": "flushed between steps (512 MiB write), outside the timed events",
+                   "parallelism": f"replicas x{world}", "host_build_s": round(build_s, 2)},
+        "roofline": roof,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": round(e2e_ms / e2e_steps, 5)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "variants": variants,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def reference_arm(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle
+    wl = WORKLOADS[args.workload]
+    p = make_poset(args.workload, 1)
+    kind, fdesc = DTYPES[args.dtype]
+    f_np = pg.function_values(p.n, 1, kind, 2)[:, 0]
+    if args.dtype == "f32c":
+        f_np = f_np.astype(np.float64)
+    rng = np.random.default_rng(7)
+    rows = rng.choice(p.n, args.steps + args.warmup, replace=False).tolist()
+    csr_t0 = time.perf_counter()
+    total = 0.0
+    for i, r in enumerate(rows):
+        t0 = time.perf_counter()
+        oracle.zeta_rows(p.n, p.src, p.dst, f_np, [r])       # one step: one exact zeta row
+        if i >= args.warmup:
+            total += time.perf_counter() - t0
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f64": "f64", "i64": "int64", "f32c": "f64"}[args.dtype], "data": "synthetic",
+            "config": {"workload": wl["desc"] + f"; f {fdesc}; B=1", "n": p.n, "k": wl["k"], "batch": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one exact zeta row per step (BFS reachability + exact sum), single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(time.perf_counter() - csr_t0, 1)}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["mz", "reference"], default="mz")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--dtype", choices=sorted(DTYPES), default="f64")
+    ap.add_argument("--variant-steps", type=int, default=50)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)          # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        device_arm(args)
+
+
+if __name__ == "__main__":
+    main()

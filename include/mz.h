@@ -1,0 +1,228 @@
+/*
+ * mz.h - fast zeta and Moebius transforms on a finite poset (C ABI).
+ *
+ * Implements, on one NVIDIA GB300 GPU (sm_103a), the O(n k) transforms of
+ * "Fast Moebius and Zeta Transforms" (Pegolotti, Seifert, Pueschel,
+ * arxiv 2211.13706):
+ *
+ *   zeta    g(x) = sum_{y <= x} f(y)               (Thm. 1 left, Cor. 1: g = Z f)
+ *   Moebius f(x) = sum_{y <= x} mu(y, x) g(y)      (Thm. 1 right, Cor. 1: f = M g = Z^-1 g)
+ *
+ * computed through the factorisation Z = U V of Sec. 3 (Eq. zfac): V is a
+ * per-chain prefix sum (Eq. zeta_cache) and U sums one entry per chain
+ * selected by the reachability map niv (Sec. 2.4, Eq. zeta-fast). The
+ * Moebius transform solves U y' = g by forward substitution and then applies
+ * V^-1 (Sec. 3 "Fast Moebius transform", Alg. 4). The transposes Z^T and M^T
+ * are the same transforms on the dual poset (all edges flipped, Sec. 2.1).
+ *
+ * A plan (mz_build) holds the one-time precomputation: topological order,
+ * chain decomposition, niv map and the processing schedule (Sec. 4). It is
+ * built on the host and uploaded to the current CUDA device once. Every
+ * transform call is then asynchronous on the caller's stream and runs only
+ * hand-written CUDA kernels.
+ *
+ * Conventions shared by every call
+ *  - Nodes are 0 .. n-1 (the caller's ids). An edge src[i] -> dst[i] means
+ *    dst[i] <= src[i] (dst is a successor of src, Sec. 2.1). Duplicate and
+ *    transitive edges are allowed; they define the same poset.
+ *  - A poset function with `batch` columns is a row-major [n][batch] array:
+ *    element (x, b) at index x * batch + b.
+ *  - MZ_I64 and MZ_F64 values are int64_t / double. MZ_F32C values are
+ *    double-word fp32 pairs stored as two planes: the hi plane ([n][batch]
+ *    floats) followed directly by the lo plane; the value is hi + lo.
+ *    Inputs with plain fp32 data pass a zero lo plane.
+ *  - int64 arithmetic wraps on overflow; keeping every partial sum inside
+ *    (-2^63, 2^63) is the caller's responsibility.
+ *  - f, g and ws are device pointers the caller owns. Input and output must
+ *    not overlap. Calls on one workspace must not overlap in time.
+ *  - Errors found on the host are returned directly and nothing is launched.
+ *    Errors found on the device (a bounded wait that ran out) are recorded in
+ *    the plan and returned by mz_check. Outputs are undefined after an error.
+ */
+#ifndef MZ_H
+#define MZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mz_stream; /* a cudaStream_t; NULL = the legacy default stream */
+
+typedef enum {
+    MZ_OK = 0,
+    MZ_ERR_INVALID_ARG = 1, /* bad size, pointer, id out of range, overlapping buffers, small workspace */
+    MZ_ERR_CYCLE = 2,       /* the edges contain a cycle or a self-loop: not a DAG (Sec. 2.1) */
+    MZ_ERR_BAD_CHAINS = 3,  /* chain_id does not partition the nodes into chains (Def. 1) */
+    MZ_ERR_OOM = 4,         /* host or device allocation failed */
+    MZ_ERR_CUDA = 5,        /* a CUDA runtime call failed (mz_last_error() has the text) */
+    MZ_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out (reported by mz_check) */
+    MZ_ERR_UNSUPPORTED = 7, /* e.g. a transpose call on a plan built without the dual */
+    MZ_ERR_NO_DEVICE = 8    /* the plan was built host-only; transforms need a device plan */
+} mz_status;
+
+typedef enum {
+    MZ_I64 = 0,  /* int64 values, exact (wrapping) arithmetic */
+    MZ_F64 = 1,  /* fp64 values, plain fp64 arithmetic */
+    MZ_F32C = 2  /* fp32 double-word pairs in and out; compensated fp32 scan and gather for
+                    zeta, fp64 chain prefixes in the Moebius forward substitution */
+} mz_dtype;
+
+typedef enum {
+    /* Moebius schedule: levels of U's own dependency graph. Alg. 4 solves U y' = g and
+       then applies V^-1; y'(x) depends only on y' at niv_j(x) for the other chains j,
+       so x can run as soon as those are done. Default. */
+    MZ_SCHED_ULEVEL = 0,
+    /* Moebius schedule of Alg. 5 / Alg. 6: antichain levels (heights), one level after
+       the other, each x computing f(x) = g(x) - sum_j y'[niv^-_j(x)] directly. */
+    MZ_SCHED_ANTICHAIN = 1
+} mz_schedule;
+
+typedef struct mz_plan mz_plan;
+
+typedef struct {
+    int32_t build_transpose;  /* nonzero: also build the dual poset's plan for mz_zeta_T / mz_mobius_T */
+    int32_t host_only;        /* nonzero: build host structures only (no device use at all) */
+    int32_t mobius_schedule;  /* an mz_schedule value */
+    int32_t reserved0;
+    int64_t spin_limit;       /* bound on polling iterations of every device-side wait; 0 = default (2^22) */
+    /* Test hook, 0 = off. v > 0 makes every transform of this plan skip one publication:
+       the look-back flag of scan tile v-1 and the y' word of the (v-1)-th row of the
+       Moebius schedule, so the waits on it run out and mz_check reports MZ_ERR_TIMEOUT. */
+    int64_t debug_withhold;
+    /* Optional allocator for the plan's device buffers (both or neither). alloc returns
+       device memory of at least `bytes` bytes, 256-byte aligned, or NULL. */
+    void *(*dev_alloc)(size_t bytes, void *ctx);
+    void (*dev_free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} mz_build_opts;
+
+typedef struct {
+    int64_t n;             /* number of elements */
+    int32_t k;             /* number of chains in the decomposition used */
+    int32_t has_transpose; /* the dual plan exists */
+    int64_t nnz;           /* nnz(N): finite entries of the niv map, self entries included (Sec. 2.4) */
+    int64_t edges;         /* distinct edges after removing duplicates */
+    int32_t levels;        /* number of antichain levels = length of the longest chain (Thm. 5) */
+    int32_t ulevels;       /* number of levels of U's dependency graph (schedule MZ_SCHED_ULEVEL) */
+    int32_t schedule;      /* the mz_schedule the plan was built for */
+    int32_t levels_T;      /* the same two numbers for the dual plan (0 without it) */
+    int32_t ulevels_T;
+    int32_t max_chain;     /* longest chain of the decomposition (q in Sec. 4) */
+    int64_t device_bytes;  /* device memory held by the plan (dual included) */
+} mz_plan_info_t;
+
+/* Arrays mz_plan_export can copy out (host memory, no device work). */
+typedef enum {
+    MZ_EXPORT_CHAIN_ID = 0, /* int32[n]: chain of each node, 0 .. k-1 */
+    MZ_EXPORT_CHAIN_POS = 1,/* int32[n]: position on its chain, 0 = bottom (smallest element) */
+    MZ_EXPORT_NIV = 2,      /* int32[n*k]: niv_j(x) as a node id, -1 for infinity, row x col j */
+    MZ_EXPORT_LEVEL = 3,    /* int32[n]: antichain level (height), 1 = minimal elements */
+    MZ_EXPORT_ULEVEL = 4,   /* int32[n]: level in U's dependency graph, 0 = no dependency */
+    MZ_EXPORT_TOPO = 5      /* int32[n]: a topological order, a largest element first */
+} mz_export;
+
+/*
+ * mz_build - the one-time precomputation for a poset (Sec. 4: Alg. 1 chain
+ * decomposition, Alg. 2 niv map via Thm. 4, Alg. 6 levels).
+ *   n         number of nodes, 1 <= n <= 2^30
+ *   m         number of edges, m >= 0
+ *   src, dst  host arrays of m node ids; edge src[i] -> dst[i] means dst[i] <= src[i]
+ *   chain_id  optional host array of n values: the caller's chain decomposition
+ *             (ids need not be dense). Each class must be totally ordered in the poset,
+ *             else MZ_ERR_BAD_CHAINS. NULL: the build computes a minimum path cover of
+ *             the DAG by maximum bipartite matching (Alg. 1). That is a chain
+ *             decomposition, but it reaches the width only when the edge set is
+ *             transitively closed.
+ *   opts      optional (NULL = defaults)
+ *   out       receives the plan; NULL on error
+ * The host arrays are only read during the call. The plan's device buffers are
+ * allocated on the current CUDA device (skipped with opts->host_only). Returns
+ * MZ_ERR_INVALID_ARG (sizes, ids out of range), MZ_ERR_CYCLE, MZ_ERR_BAD_CHAINS,
+ * MZ_ERR_OOM or MZ_ERR_CUDA; nothing leaks on error.
+ */
+mz_status mz_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                   const int32_t *chain_id, const mz_build_opts *opts, mz_plan **out);
+
+/* Frees the plan and its device buffers (synchronises the device first). NULL is a no-op. */
+void mz_destroy(mz_plan *plan);
+
+/*
+ * mz_workspace_size - bytes of device scratch every transform of this plan needs
+ * for `dtype` and `batch` (transposes included). The workspace holds the chain
+ * prefix array y' (Sec. 3, x' of Alg. 3 / y' of Alg. 4) and the scan's look-back state; it
+ * needs 256-byte alignment and no initialisation.
+ */
+mz_status mz_workspace_size(const mz_plan *plan, mz_dtype dtype, int32_t batch, size_t *bytes);
+
+/*
+ * mz_zeta - g = Z f (Thm. 1 left). Two kernels: the per-chain prefix scan
+ * c = V f (Eq. zeta_cache; decoupled look-back across tiles) and the gather
+ * g(x) = sum_j c[niv_j(x)] (Eq. zeta-fast).
+ *   f   device, [n][batch] input (F32C: 2 planes)
+ *   g   device, [n][batch] output (F32C: 2 planes)
+ *   ws  device workspace of ws_bytes >= mz_workspace_size(plan, dtype, batch)
+ * Asynchronous on `stream`. batch >= 1.
+ */
+mz_status mz_zeta(const mz_plan *plan, mz_dtype dtype, const void *f, void *g, int32_t batch,
+                  void *ws, size_t ws_bytes, mz_stream stream);
+
+/*
+ * mz_mobius - f = M g (Thm. 1 right) by the fast Moebius transform of Sec. 3:
+ * forward substitution y'(x) = g(x) - sum_{j != id(x)} y'(niv_j(x)) in a
+ * persistent kernel that follows the plan's schedule, then f(x) = y'(x) -
+ * y'(next(x)) (V^-1). Arguments as for mz_zeta (g in, f out).
+ */
+mz_status mz_mobius(const mz_plan *plan, mz_dtype dtype, const void *g, void *f, int32_t batch,
+                    void *ws, size_t ws_bytes, mz_stream stream);
+
+/* mz_zeta_T - r = Z^T h: r(y) = sum_{x : y <= x} h(x), the zeta transform of the dual
+   poset. Needs a plan built with build_transpose, else MZ_ERR_UNSUPPORTED. */
+mz_status mz_zeta_T(const mz_plan *plan, mz_dtype dtype, const void *h, void *r, int32_t batch,
+                    void *ws, size_t ws_bytes, mz_stream stream);
+
+/* mz_mobius_T - r = M^T h, the Moebius transform of the dual poset. As mz_zeta_T. */
+mz_status mz_mobius_T(const mz_plan *plan, mz_dtype dtype, const void *h, void *r, int32_t batch,
+                      void *ws, size_t ws_bytes, mz_stream stream);
+
+/*
+ * mz_check - synchronises `stream`, then returns and clears the plan's device-side
+ * status word, which every transform of the plan sets when one of its bounded waits
+ * runs out (MZ_OK or MZ_ERR_TIMEOUT; the word is shared by all calls of the plan).
+ * MZ_ERR_CUDA if the stream reports an error.
+ */
+mz_status mz_check(const mz_plan *plan, mz_stream stream);
+
+/* Fills *info (host data only). */
+mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info);
+
+/* Copies one host-side array of the plan (mz_export) into `out` (`bytes` long).
+   `dual` nonzero selects the dual plan. MZ_ERR_INVALID_ARG if `bytes` is too small. */
+mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *out, size_t bytes);
+
+/* Kernel launches issued by the last transform call on this thread (memsets excluded). */
+int32_t mz_last_launch_count(void);
+
+/*
+ * Profiling hook. While `events` is non-NULL, every transform call on this thread
+ * records events[0] on its stream before its first device operation and events[i]
+ * right after its i-th kernel launch (i = 1 .. launches), skipping indices at or
+ * beyond `capacity`. The events are the caller's cudaEvent_t handles (created with
+ * timing enabled); the library never creates, waits on or destroys them. NULL (or
+ * capacity 0) turns the hook off. Timing only: results are unaffected.
+ */
+void mz_set_launch_events(void *const *events, int32_t capacity);
+
+/* Static text for a status code. */
+const char *mz_status_string(mz_status s);
+
+/* Detail of the last error on this thread (empty string if none). */
+const char *mz_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MZ_H */

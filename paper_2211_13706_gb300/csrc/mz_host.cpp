@@ -1,0 +1,272 @@
+// Host-side precomputation of a plan (arxiv 2211.13706, Sec. 2.3, 2.4, 4).
+//
+//   1. validate the edge list and remove duplicates;
+//   2. topological order by Kahn's algorithm (Sec. 2.1: x < y puts x after y);
+//   3. a chain decomposition (Def. 1): the caller's, or a minimum path cover
+//      of the DAG by maximum bipartite matching (Alg. 1, Hopcroft-Karp);
+//   4. the slot layout of the chain prefix array (see mz_internal.h);
+//   5. the niv map by Thm. 4 (Alg. 2), bottom-up, with the caller's chains
+//      checked on the way;
+//   6. antichain levels (Alg. 6, heights) and the levels of U's dependency
+//      graph (the schedule of the forward substitution of Alg. 4).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "mz_internal.h"
+
+namespace mz {
+
+namespace {
+
+// Hopcroft-Karp maximum matching between "upper" copies (edge sources) and
+// "lower" copies (edge targets) of the nodes (Alg. 1's bipartite graph G').
+// Returns next_of[u] = the node matched below u, or -1.
+std::vector<int32_t> max_matching(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int32_t> &adj) {
+    const int32_t NIL = -1;
+    std::vector<int32_t> mate_u(n, NIL), mate_v(n, NIL), dist(n), queue(n);
+    std::vector<int64_t> it(n);
+    std::vector<int32_t> stack;
+    // greedy start
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e)
+            if (mate_v[adj[e]] == NIL) { mate_u[u] = adj[e]; mate_v[adj[e]] = (int32_t)u; break; }
+    const int32_t INF = INT32_MAX;
+    while (true) {
+        // BFS from free upper nodes over alternating paths
+        int64_t qh = 0, qt = 0;
+        bool found = false;
+        for (int64_t u = 0; u < n; ++u) {
+            if (mate_u[u] == NIL) { dist[u] = 0; queue[qt++] = (int32_t)u; }
+            else dist[u] = INF;
+        }
+        while (qh < qt) {
+            int32_t u = queue[qh++];
+            for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e) {
+                int32_t w = mate_v[adj[e]];
+                if (w == NIL) found = true;
+                else if (dist[w] == INF) { dist[w] = dist[u] + 1; queue[qt++] = w; }
+            }
+        }
+        if (!found) break;
+        // iterative DFS along the layered graph
+        for (int64_t u = 0; u < n; ++u) it[u] = ptr[u];
+        for (int64_t s = 0; s < n; ++s) {
+            if (mate_u[s] != NIL) continue;
+            stack.clear();
+            stack.push_back((int32_t)s);
+            while (!stack.empty()) {
+                int32_t u = stack.back();
+                bool advanced = false;
+                while (it[u] < ptr[u + 1]) {
+                    int32_t v = adj[it[u]];
+                    int32_t w = mate_v[v];
+                    if (w == NIL) {
+                        // augment along the stack: each stacked node takes the edge it[] points at
+                        for (size_t i = stack.size(); i-- > 0;) {
+                            int32_t a = stack[i];
+                            int32_t b = adj[it[a]];
+                            mate_u[a] = b;
+                            mate_v[b] = a;
+                        }
+                        stack.clear();
+                        advanced = true;
+                        break;
+                    }
+                    if (dist[w] == dist[u] + 1) { stack.push_back(w); advanced = true; break; }
+                    ++it[u];
+                }
+                if (!advanced) {           // dead end: drop u from the layered graph
+                    dist[u] = INF;
+                    stack.pop_back();
+                    if (!stack.empty()) ++it[stack.back()];
+                }
+            }
+        }
+    }
+    return mate_u;
+}
+
+}  // namespace
+
+mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const std::vector<int32_t> &dst_in,
+                          const int32_t *chain_in, HostSide &H, std::string &err) {
+    H = HostSide();
+    H.n = n;
+    const int64_t m = (int64_t)src_in.size();
+    // ---- 1. validate, dedupe, CSR of children
+    for (int64_t i = 0; i < m; ++i) {
+        if (src_in[i] < 0 || src_in[i] >= n || dst_in[i] < 0 || dst_in[i] >= n) {
+            err = "edge " + std::to_string(i) + " has a node id outside [0, n)";
+            return MZ_ERR_INVALID_ARG;
+        }
+        if (src_in[i] == dst_in[i]) {
+            err = "edge " + std::to_string(i) + " is a self-loop";
+            return MZ_ERR_CYCLE;
+        }
+    }
+    std::vector<int64_t> ptr(n + 1, 0);
+    for (int64_t i = 0; i < m; ++i) ptr[src_in[i] + 1]++;
+    for (int64_t x = 0; x < n; ++x) ptr[x + 1] += ptr[x];
+    std::vector<int32_t> adj(m);
+    {
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t i = 0; i < m; ++i) adj[fill[src_in[i]]++] = dst_in[i];
+    }
+    {   // sort + unique each child list, compact
+        int64_t w = 0;
+        for (int64_t x = 0; x < n; ++x) {
+            int64_t b = ptr[x], e = ptr[x + 1];
+            std::sort(adj.begin() + b, adj.begin() + e);
+            int64_t start = w;
+            for (int64_t i = b; i < e; ++i)
+                if (i == b || adj[i] != adj[i - 1]) adj[w++] = adj[i];
+            ptr[x] = start;
+        }
+        ptr[n] = w;
+        adj.resize(w);
+    }
+    H.edges = (int64_t)adj.size();
+
+    // ---- 2. Kahn's algorithm from the maximal elements
+    std::vector<int32_t> indeg(n, 0);
+    for (int32_t v : adj) indeg[v]++;
+    H.topo.resize(n);
+    int64_t head = 0, tail = 0;
+    for (int64_t x = 0; x < n; ++x)
+        if (indeg[x] == 0) H.topo[tail++] = (int32_t)x;
+    while (head < tail) {
+        int32_t x = H.topo[head++];
+        for (int64_t e = ptr[x]; e < ptr[x + 1]; ++e)
+            if (--indeg[adj[e]] == 0) H.topo[tail++] = adj[e];
+    }
+    if (tail != n) {
+        err = "the edges contain a cycle";
+        return MZ_ERR_CYCLE;
+    }
+    std::vector<int32_t> pos(n);
+    for (int64_t i = 0; i < n; ++i) pos[H.topo[i]] = (int32_t)i;
+
+    // ---- 3. chain decomposition
+    H.chain_id.assign(n, -1);
+    std::vector<std::vector<int32_t>> chains;  // members, bottom first
+    if (chain_in) {
+        std::vector<int32_t> ids(chain_in, chain_in + n);
+        std::vector<int32_t> uniq(ids);
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        chains.resize(uniq.size());
+        for (int64_t x = 0; x < n; ++x) {
+            int32_t c = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), ids[x]) - uniq.begin());
+            H.chain_id[x] = c;
+        }
+        // members in topological order, reversed (bottom first)
+        for (int64_t i = n - 1; i >= 0; --i) chains[H.chain_id[H.topo[i]]].push_back(H.topo[i]);
+    } else {
+        std::vector<int32_t> next = max_matching(n, ptr, adj);
+        std::vector<char> has_pred(n, 0);
+        for (int64_t u = 0; u < n; ++u)
+            if (next[u] >= 0) has_pred[next[u]] = 1;
+        for (int64_t i = 0; i < n; ++i) {       // chain heads in topological order
+            int32_t x = H.topo[i];
+            if (has_pred[x]) continue;
+            std::vector<int32_t> members;
+            for (int32_t y = x; y >= 0; y = next[y]) members.push_back(y);
+            std::reverse(members.begin(), members.end());
+            for (int32_t y : members) H.chain_id[y] = (int32_t)chains.size();
+            chains.push_back(std::move(members));
+        }
+    }
+    const int64_t k = (int64_t)chains.size();
+    if (k < 1 || n + k > (int64_t)INT32_MAX) {
+        err = "too many nodes plus chains for 32-bit slot indices";
+        return MZ_ERR_INVALID_ARG;
+    }
+    H.k = (int32_t)k;
+
+    // ---- 4. slot layout
+    H.chain_base.assign(k + 1, 0);
+    H.chain_pos.assign(n, 0);
+    H.node_slot.assign(n, 0);
+    H.slot_node.assign(n + k, -1);
+    H.row_node.assign(n, 0);
+    {
+        int64_t base = 0, row = 0;
+        for (int64_t c = 0; c < k; ++c) {
+            H.chain_base[c] = base;
+            H.max_chain = std::max<int32_t>(H.max_chain, (int32_t)chains[c].size());
+            for (size_t p = 0; p < chains[c].size(); ++p) {
+                int32_t x = chains[c][p];
+                H.chain_pos[x] = (int32_t)p;
+                H.node_slot[x] = (int32_t)(base + 1 + (int64_t)p);
+                H.slot_node[base + 1 + p] = x;
+                H.row_node[row++] = x;
+            }
+            base += (int64_t)chains[c].size() + 1;
+        }
+        H.chain_base[k] = base;
+    }
+
+    // ---- 5. niv map by Thm. 4, bottom-up. Entry (x, c) = slot of niv_c(x), or base_c.
+    // The caller's chains are checked here: the element below x on its chain, or the
+    // chain's zero slot when x is the bottom, must be exactly the highest element of
+    // x's chain reachable through x's children.
+    try {
+        H.N.assign((size_t)n * (size_t)k, 0);
+    } catch (...) {
+        err = "host allocation of the niv map failed";
+        return MZ_ERR_OOM;
+    }
+    std::vector<int32_t> base32(k), cur(k);
+    for (int64_t c = 0; c < k; ++c) base32[c] = (int32_t)H.chain_base[c];
+    std::vector<int32_t> kids;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int32_t x = H.topo[i];
+        std::memcpy(cur.data(), base32.data(), sizeof(int32_t) * k);
+        kids.assign(adj.begin() + ptr[x], adj.begin() + ptr[x + 1]);
+        // highest children first: a child already covered adds nothing (G3 pruning)
+        std::sort(kids.begin(), kids.end(), [&](int32_t a, int32_t b) { return pos[a] < pos[b]; });
+        for (int32_t z : kids) {
+            const int32_t cz = H.chain_id[z];
+            if (cur[cz] >= H.node_slot[z]) continue;
+            const int32_t *row = &H.N[(size_t)(H.node_slot[z] - cz - 1) * k];
+            for (int64_t c = 0; c < k; ++c) cur[c] = std::max(cur[c], row[c]);
+        }
+        const int32_t cx = H.chain_id[x];
+        const int32_t sx = H.node_slot[x];
+        if (cur[cx] != sx - 1) {
+            err = "chain " + std::to_string(cx) + " is not totally ordered at node " + std::to_string(x);
+            return MZ_ERR_BAD_CHAINS;
+        }
+        cur[cx] = sx;
+        std::memcpy(&H.N[(size_t)(sx - cx - 1) * k], cur.data(), sizeof(int32_t) * k);
+    }
+    H.nnz = 0;
+    for (int64_t r = 0; r < n; ++r) {
+        const int32_t *row = &H.N[(size_t)r * k];
+        for (int64_t c = 0; c < k; ++c) H.nnz += row[c] != base32[c];
+    }
+
+    // ---- 6. levels
+    H.level.assign(n, 1);
+    H.ulevel.assign(n, 0);
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int32_t x = H.topo[i];
+        int32_t h = 0;
+        for (int64_t e = ptr[x]; e < ptr[x + 1]; ++e) h = std::max(h, H.level[adj[e]]);
+        H.level[x] = h + 1;
+        const int32_t cx = H.chain_id[x];
+        const int32_t *row = &H.N[(size_t)(H.node_slot[x] - cx - 1) * k];
+        int32_t u = 0;
+        for (int64_t c = 0; c < k; ++c)
+            if (c != cx && row[c] != base32[c]) u = std::max(u, H.ulevel[H.slot_node[row[c]]] + 1);
+        H.ulevel[x] = u;
+    }
+    H.nlevels = *std::max_element(H.level.begin(), H.level.end());
+    H.nulevels = *std::max_element(H.ulevel.begin(), H.ulevel.end()) + 1;
+    return MZ_OK;
+}
+
+}  // namespace mz

@@ -1,0 +1,82 @@
+// Internal plan layout shared by the host build (mz_host.cpp) and the CUDA
+// side (mz_abi.cu, mz_kernels.cu). Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mz.h"
+
+namespace mz {
+
+// Rows of the niv map are stored in *slot order*: chain 0 bottom -> top, then
+// chain 1, and so on. The prefix array y' has n + k slots: chain c owns slots
+// [base_c, base_c + len_c], where base_c = sum_{c' < c} len_{c'} + c holds a
+// constant 0 (it stands for niv_c(x) = infinity), and the element at chain
+// position p (0 = bottom) sits at slot base_c + 1 + p. Row r of the map is the
+// element at slot r + c + 1. Every map entry is a slot index, so the gather
+// needs no branch for infinity.
+constexpr int kTileRows = 32;  // rows per tile of the tiled (column-major within a tile) map
+
+struct HostSide {
+    int64_t n = 0;
+    int32_t k = 0;
+    int64_t edges = 0;          // distinct edges
+    int64_t nnz = 0;            // finite niv entries (self entries included)
+    int32_t nlevels = 0;        // antichain levels (heights)
+    int32_t nulevels = 0;       // levels of U's dependency graph
+    int32_t max_chain = 0;
+    std::vector<int32_t> topo;       // [n] topological order, a largest element first
+    std::vector<int32_t> chain_id;   // [n]
+    std::vector<int32_t> chain_pos;  // [n] 0 = bottom
+    std::vector<int64_t> chain_base; // [k + 1], chain_base[k] = n + k
+    std::vector<int32_t> node_slot;  // [n]
+    std::vector<int32_t> slot_node;  // [n + k], -1 at zero slots
+    std::vector<int32_t> row_node;   // [n] node of row r
+    std::vector<int32_t> N;          // [n][k] by row, slot indices
+    std::vector<int32_t> level;      // [n] heights, 1 = minimal
+    std::vector<int32_t> ulevel;     // [n] 0 = no dependency on another chain
+};
+
+// Device copies of one side (primal or dual).
+struct DeviceSide {
+    int32_t *slot_node = nullptr;  // [n + k]
+    int32_t *Nt = nullptr;         // [ntiles][k][32] tiled map for the zeta gather
+    int32_t *row_node = nullptr;   // [ntiles * 32], -1 for padding rows
+    int32_t *Nm = nullptr;         // [n][k] rows in Moebius processing order; own column -> zero slot
+    int32_t *mob_node = nullptr;   // [n] node of the i-th processed row
+    int32_t *mob_slot = nullptr;   // [n] its slot
+    int64_t ntiles = 0;
+};
+
+}  // namespace mz
+
+struct mz_plan {
+    mz::HostSide host[2];
+    mz::DeviceSide dev[2];
+    bool has_dual = false;
+    bool host_only = false;
+    int32_t schedule = MZ_SCHED_ULEVEL;
+    int64_t spin_limit = 1ll << 22;
+    int64_t withhold = -1;          // test hook (see mz_build_opts::debug_withhold)
+    uint32_t *d_status = nullptr;   // device status word (MZ_OK / MZ_ERR_TIMEOUT)
+    int device = -1;
+    int num_sms = 0;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocations;
+    void *(*dev_alloc)(size_t, void *) = nullptr;
+    void (*dev_free)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+};
+
+namespace mz {
+
+// Host build of one side: validates, orders, decomposes into chains, builds
+// the niv map (Thm. 4) and both level structures. chain_in may be null.
+mz_status build_host_side(int64_t n, const std::vector<int32_t> &src, const std::vector<int32_t> &dst,
+                          const int32_t *chain_in, HostSide &H, std::string &err);
+
+void set_last_error(const std::string &s);
+
+}  // namespace mz

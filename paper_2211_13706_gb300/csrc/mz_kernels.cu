@@ -1,0 +1,451 @@
+// CUDA kernels of the transforms (sm_103a) and their launchers.
+//
+//   k_chain_scan   c = V f, the per-chain prefix sums of Eq. (zeta_cache), as one
+//                  segmented inclusive scan over the slot array with a zero slot
+//                  in front of every chain; single pass, decoupled look-back
+//                  between tiles (Merrill & Garland, "Single-pass parallel prefix
+//                  scan with decoupled look-back", 2016).
+//   k_niv_gather   g(x) = sum_j c[niv_j(x)], Eq. (zeta-fast) = U c. One warp per
+//                  tile of 32 consecutive rows (one row per lane), the tiled map
+//                  streamed with coalesced loads; along a chain niv_j is monotone,
+//                  so a warp's 32 gathers of one column hit a narrow window of c.
+//   k_mob_init     fills y' with the "not ready" sentinel (0 at zero slots).
+//   k_mob_wave     forward substitution of Alg. 4, U y' = g:
+//                  y'(x) = g(x) - sum_{j != id(x)} y'(niv_j(x)),
+//                  persistent (cooperative launch), one warp per row in the
+//                  schedule's order; every read of y' polls until the word is
+//                  no longer the sentinel, with a bounded number of polls.
+//                  Antichain schedule (Alg. 5/6): f(x) = g(x) - sum_j y'[niv^-_j(x)]
+//                  and y'(x) = y'(next(x)) + f(x) (Sec. 3, V^-1 folded in).
+//   k_mob_diff     f(x) = y'(x) - y'(next(x)): V^-1 (Sec. 3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "mz_arith.cuh"
+#include "mz_kernels.h"
+
+namespace mz {
+
+// ---------------------------------------------------------------- memory-model helpers
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void report(uint32_t *status, uint32_t code) { atomicCAS(status, 0u, code); }
+
+// Wait until *flag != 0 (acquire). Gives up after `limit` polls, or early once
+// another wait has recorded an error; returns 0 then.
+__device__ uint32_t wait_flag(const uint32_t *flag, uint32_t *status, int64_t limit) {
+    for (int64_t it = 0;; ++it) {
+        uint32_t v = ld_acquire_u32(flag);
+        if (v) return v;
+        if ((it & 255) == 255 && ld_relaxed_u32(status)) return 0;
+        if (it >= limit) {
+            report(status, MZ_ERR_TIMEOUT);
+            return 0;
+        }
+        __nanosleep(32);
+    }
+}
+
+// Wait until *p != sentinel; returns the word (0 after a timeout or an abort).
+__device__ __forceinline__ unsigned long long wait_value(const unsigned long long *p, unsigned long long sentinel,
+                                                         uint32_t *status, int64_t limit) {
+    unsigned long long v = ld_relaxed_u64(p);
+    if (v != sentinel) return v;
+    for (int64_t it = 0;; ++it) {
+        v = ld_relaxed_u64(p);
+        if (v != sentinel) return v;
+        if ((it & 255) == 255 && ld_relaxed_u32(status)) return 0;
+        if (it >= limit) {
+            report(status, MZ_ERR_TIMEOUT);
+            return 0;
+        }
+        if (it > 64) __nanosleep(64);
+    }
+}
+
+// ---------------------------------------------------------------- chain scan (V f)
+constexpr int kScanThreads = 256;
+constexpr int kScanSeg = 16;  // slots per thread
+
+template <class Pol>
+__global__ void __launch_bounds__(kScanThreads) k_chain_scan(ScanArgs a) {
+    using P_t = typename Pol::P_t;
+    __shared__ uint32_t s_tile;
+    __shared__ int s_has_reset;
+    __shared__ unsigned char s_flag[kScanThreads];
+    __shared__ P_t s_val[kScanThreads];
+    __shared__ P_t s_excl[32];
+
+    const int t = threadIdx.x;
+    const int group = blockIdx.y;
+    if (t == 0) {
+        s_tile = atomicAdd(&a.counters[group], 1u);   // tiles start in order: look-back never waits on an unstarted tile
+        s_has_reset = 0;
+    }
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int BW = a.BW, R = a.R;
+    const int col = t % BW, r = t / BW;
+    const bool active = r < R;
+    const int64_t b = (int64_t)group * BW + col;
+    const bool colok = active && b < a.B;
+    const int64_t slot0 = tile * (int64_t)R * kScanSeg + (int64_t)r * kScanSeg;
+
+    P_t vals[kScanSeg];
+    P_t acc = Pol::zero();
+    int first_reset = kScanSeg;
+#pragma unroll
+    for (int j = 0; j < kScanSeg; ++j) {
+        const int64_t s = slot0 + j;
+        if (colok && s < a.nslots) {
+            const int32_t node = a.slot_node[s];
+            if (node < 0) {                        // zero slot: a chain starts here
+                acc = Pol::zero();
+                if (first_reset == kScanSeg) first_reset = j;
+            } else {
+                acc = Pol::scan_add(acc, Pol::load_in(a.f, (int64_t)node * a.B + b, a.nB));
+            }
+        }
+        vals[j] = acc;
+    }
+    const bool seg_reset = first_reset < kScanSeg;
+    if (seg_reset) s_has_reset = 1;
+    s_flag[t] = seg_reset;
+    s_val[t] = acc;
+    __syncthreads();
+    // inclusive segmented scan over the R sub-threads of each column (Hillis-Steele)
+    for (int d = 1; d < R; d <<= 1) {
+        const bool take = active && r >= d;
+        unsigned char of = 0;
+        P_t ov = Pol::zero();
+        if (take) {
+            of = s_flag[t - d * BW];
+            ov = s_val[t - d * BW];
+        }
+        __syncthreads();
+        if (take && !s_flag[t]) {
+            s_val[t] = Pol::scan_add(ov, s_val[t]);
+            s_flag[t] = of;
+        }
+        __syncthreads();
+    }
+    unsigned char ef = 0;
+    P_t ev = Pol::zero();
+    if (active && r > 0) {
+        ef = s_flag[t - BW];
+        ev = s_val[t - BW];
+    }
+
+    if (t < 32) {
+        const int lane = t;
+        const int64_t me = (int64_t)group * a.ntiles + tile;
+        const bool has_reset = s_has_reset != 0;   // same for every column: resets sit at zero slots
+        P_t tagg = Pol::zero();
+        if (lane < BW) tagg = s_val[(R - 1) * BW + lane];
+        P_t *agg = reinterpret_cast<P_t *>(a.agg);
+        P_t *inc = reinterpret_cast<P_t *>(a.inc);
+        const bool withhold = (me == a.withhold);
+        // publish the tile aggregate, or directly its inclusive value when it holds a chain start
+        if (lane < BW) {
+            (has_reset ? inc : agg)[me * BW + lane] = tagg;
+            __threadfence();
+        }
+        __syncwarp();
+        if (lane == 0 && !withhold) st_release_u32(&a.flags[me], has_reset ? 2u : 1u);
+        // look-back over the predecessors of this tile in the same column group
+        P_t excl = Pol::zero();
+        if (tile > 0) {
+            int64_t pred = tile - 1;
+            while (true) {
+                const int64_t pid = (int64_t)group * a.ntiles + pred;
+                const uint32_t fl = wait_flag(&a.flags[pid], a.status, a.spin_limit);
+                if (fl == 2u) {
+                    if (lane < BW) excl = Pol::scan_add(inc[pid * BW + lane], excl);
+                    break;
+                }
+                if (fl == 1u) {
+                    if (lane < BW) excl = Pol::scan_add(agg[pid * BW + lane], excl);
+                    if (pred == 0) break;
+                    --pred;
+                    continue;
+                }
+                break;   // timed out or aborted
+            }
+        }
+        if (!has_reset) {
+            if (lane < BW) {
+                inc[me * BW + lane] = Pol::scan_add(excl, tagg);
+                __threadfence();
+            }
+            __syncwarp();
+            if (lane == 0 && !withhold) st_release_u32(&a.flags[me], 2u);
+        }
+        if (lane < BW) s_excl[lane] = excl;
+    }
+    __syncthreads();
+
+    if (colok) {
+        const P_t pre = ef ? ev : Pol::scan_add(s_excl[col], ev);
+        P_t *P = reinterpret_cast<P_t *>(a.P);
+#pragma unroll
+        for (int j = 0; j < kScanSeg; ++j) {
+            const int64_t s = slot0 + j;
+            if (s < a.nslots) P[s * a.B + b] = (j < first_reset) ? Pol::scan_add(pre, vals[j]) : vals[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- niv gather (U c)
+constexpr int kGatherThreads = 256;
+
+template <class Pol, int BT>
+__global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
+    using P_t = typename Pol::P_t;
+    using Acc = typename Pol::Acc;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t b0 = (int64_t)blockIdx.y * BT;
+    const P_t *__restrict__ P = reinterpret_cast<const P_t *>(a.P);
+    const int k = a.k;
+    for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
+        const int32_t *__restrict__ np = a.Nt + tile * (int64_t)k * kTileRows + lane;
+        Acc acc[BT];
+#pragma unroll
+        for (int u = 0; u < BT; ++u) acc[u] = Pol::acc_zero();
+        int c = 0;
+        for (; c + 8 <= k; c += 8) {
+            int32_t s[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s[u] = __ldcs(np + (int64_t)(c + u) * kTileRows);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int q = 0; q < BT; ++q)
+                    if (BT == 1 || b0 + q < a.B) Pol::acc_add(acc[q], __ldg(P + (int64_t)s[u] * a.B + b0 + q));
+        }
+        for (; c < k; ++c) {
+            const int32_t s = __ldcs(np + (int64_t)c * kTileRows);
+#pragma unroll
+            for (int q = 0; q < BT; ++q)
+                if (BT == 1 || b0 + q < a.B) Pol::acc_add(acc[q], __ldg(P + (int64_t)s * a.B + b0 + q));
+        }
+        const int32_t node = a.row_node[tile * kTileRows + lane];
+        if (node >= 0) {
+#pragma unroll
+            for (int q = 0; q < BT; ++q)
+                if (BT == 1 || b0 + q < a.B) Pol::store_out(a.g, (int64_t)node * a.B + b0 + q, a.nB, acc[q]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Moebius
+template <class M>
+__global__ void k_mob_init(const int32_t *__restrict__ slot_node, int64_t nslots, int32_t B,
+                           unsigned long long *__restrict__ P) {
+    const int64_t total = nslots * B;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        P[i] = slot_node[i / B] < 0 ? 0ull : M::kSentinel;
+}
+
+template <class T>
+__device__ __forceinline__ T shfl_xor_t(T v, int off) {
+    return __shfl_xor_sync(0xffffffffu, v, off);
+}
+
+template <class M, bool ANTI>
+__global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
+    using T = typename M::T;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int k = a.k;
+    const int32_t B = a.B;
+    unsigned long long *P = a.P;
+    const unsigned long long SENT = M::kSentinel;
+    for (int64_t i = warp; i < a.n; i += nwarps) {
+        const int32_t *__restrict__ row = a.Nm + i * (int64_t)k;
+        const int64_t node = a.mob_node[i];
+        const int64_t sout = a.mob_slot[i];
+        const bool publish = (i != a.withhold);
+        if (B == 1) {
+            T acc = T(0);
+            for (int c = lane; c < k; c += 32)
+                acc = M::add(acc, M::from_bits(wait_value(P + row[c], SENT, a.status, a.spin_limit)));
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) acc = M::add(acc, shfl_xor_t(acc, off));
+            if (lane == 0) {
+                const T gx = M::load_in(a.g, node, a.nB);
+                if (ANTI) {
+                    const T prev = M::from_bits(wait_value(P + sout - 1, SENT, a.status, a.spin_limit));
+                    const T fx = M::sub(gx, M::add(acc, prev));
+                    if (publish) st_relaxed_u64(P + sout, M::to_bits(M::add(prev, fx)));
+                    M::store_out(a.f, node, a.nB, fx);
+                } else if (publish) {
+                    st_relaxed_u64(P + sout, M::to_bits(M::sub(gx, acc)));
+                }
+            }
+        } else if (B <= 32 && (B & (B - 1)) == 0) {
+            const int bl = lane & (B - 1);
+            const int cstep = 32 / B;
+            T acc = T(0);
+            for (int c = lane / B; c < k; c += cstep)
+                acc = M::add(acc, M::from_bits(wait_value(P + (int64_t)row[c] * B + bl, SENT, a.status, a.spin_limit)));
+            for (int off = 16; off >= B; off >>= 1) acc = M::add(acc, shfl_xor_t(acc, off));
+            if (lane < B) {
+                const T gx = M::load_in(a.g, node * B + bl, a.nB);
+                if (ANTI) {
+                    const T prev = M::from_bits(wait_value(P + (sout - 1) * B + bl, SENT, a.status, a.spin_limit));
+                    const T fx = M::sub(gx, M::add(acc, prev));
+                    if (publish) st_relaxed_u64(P + sout * B + bl, M::to_bits(M::add(prev, fx)));
+                    M::store_out(a.f, node * B + bl, a.nB, fx);
+                } else if (publish) {
+                    st_relaxed_u64(P + sout * B + bl, M::to_bits(M::sub(gx, acc)));
+                }
+            }
+        } else {
+            for (int64_t bl = lane; bl < B; bl += 32) {
+                T acc = T(0);
+                for (int c = 0; c < k; ++c)
+                    acc = M::add(acc, M::from_bits(wait_value(P + (int64_t)row[c] * B + bl, SENT, a.status, a.spin_limit)));
+                const T gx = M::load_in(a.g, node * B + bl, a.nB);
+                if (ANTI) {
+                    const T prev = M::from_bits(wait_value(P + (sout - 1) * B + bl, SENT, a.status, a.spin_limit));
+                    const T fx = M::sub(gx, M::add(acc, prev));
+                    if (publish) st_relaxed_u64(P + sout * B + bl, M::to_bits(M::add(prev, fx)));
+                    M::store_out(a.f, node * B + bl, a.nB, fx);
+                } else if (publish) {
+                    st_relaxed_u64(P + sout * B + bl, M::to_bits(M::sub(gx, acc)));
+                }
+            }
+        }
+    }
+}
+
+template <class M>
+__global__ void k_mob_diff(const int32_t *__restrict__ slot_node, int64_t nslots, int32_t B,
+                           const unsigned long long *__restrict__ P, void *f, int64_t nB) {
+    const int64_t total = nslots * B;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / B;
+        const int32_t node = slot_node[s];
+        if (node < 0) continue;
+        const int64_t bl = i - s * B;
+        // slot s - 1 is next(x) on the same chain, or the chain's zero slot
+        const typename M::T y = M::from_bits(P[i]);
+        const typename M::T yp = M::from_bits(P[i - B]);
+        M::store_out(f, (int64_t)node * B + bl, nB, M::sub(y, yp));
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+ScanShape scan_shape(int64_t nslots, int32_t B) {
+    ScanShape sh;
+    sh.BW = B < 32 ? B : 32;
+    sh.R = kScanThreads / sh.BW;
+    sh.groups = (B + sh.BW - 1) / sh.BW;
+    sh.tile_slots = (int64_t)sh.R * kScanSeg;
+    sh.ntiles = (nslots + sh.tile_slots - 1) / sh.tile_slots;
+    return sh;
+}
+
+template <class Pol>
+static cudaError_t launch_scan_t(const ScanArgs &a, const ScanShape &sh, cudaStream_t st) {
+    dim3 grid((unsigned)sh.ntiles, (unsigned)sh.groups);
+    k_chain_scan<Pol><<<grid, kScanThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(int dtype, const ScanArgs &a, const ScanShape &sh, cudaStream_t st) {
+    switch (dtype) {
+        case MZ_I64: return launch_scan_t<PolI64>(a, sh, st);
+        case MZ_F64: return launch_scan_t<PolF64>(a, sh, st);
+        default: return launch_scan_t<PolF32C>(a, sh, st);
+    }
+}
+
+template <class Pol>
+static cudaError_t launch_gather_t(const GatherArgs &a, int num_sms, cudaStream_t st) {
+    const int warps_per_block = kGatherThreads / 32;
+    int64_t blocks = (a.ntiles + warps_per_block - 1) / warps_per_block;
+    blocks = std::min<int64_t>(blocks, (int64_t)num_sms * 32);
+    if (a.B == 1) {
+        k_niv_gather<Pol, 1><<<dim3((unsigned)blocks, 1), kGatherThreads, 0, st>>>(a);
+    } else {
+        const unsigned gy = (unsigned)((a.B + 3) / 4);
+        k_niv_gather<Pol, 4><<<dim3((unsigned)blocks, gy), kGatherThreads, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(int dtype, const GatherArgs &a, int num_sms, cudaStream_t st) {
+    switch (dtype) {
+        case MZ_I64: return launch_gather_t<PolI64>(a, num_sms, st);
+        case MZ_F64: return launch_gather_t<PolF64>(a, num_sms, st);
+        default: return launch_gather_t<PolF32C>(a, num_sms, st);
+    }
+}
+
+template <class M>
+static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, int64_t nslots, bool anti,
+                                   int num_sms, cudaStream_t st, int *launches) {
+    const int64_t total = nslots * a.B;
+    const unsigned eblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 16));
+    k_mob_init<M><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mark_event(++*launches, st);
+    // persistent wavefront: every block resident (cooperative launch), one warp per row
+    void *fn = anti ? (void *)k_mob_wave<M, true> : (void *)k_mob_wave<M, false>;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (int64_t)std::max(1, per_sm) * num_sms;
+    blocks = std::min<int64_t>(blocks, (a.n + 7) / 8);
+    blocks = std::max<int64_t>(blocks, 1);
+    MobArgs args = a;
+    void *params[] = {&args};
+    e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(256), params, 0, st);
+    if (e != cudaSuccess) return e;
+    mark_event(++*launches, st);
+    if (!anti) {
+        k_mob_diff<M><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P, a.f, a.nB);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        mark_event(++*launches, st);
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_mobius(int dtype, const MobArgs &a, const int32_t *slot_node, int64_t nslots, bool anti,
+                          int num_sms, cudaStream_t st, int *launches) {
+    switch (dtype) {
+        case MZ_I64: return launch_mobius_t<MobI64>(a, slot_node, nslots, anti, num_sms, st, launches);
+        case MZ_F64: return launch_mobius_t<MobF64>(a, slot_node, nslots, anti, num_sms, st, launches);
+        default: return launch_mobius_t<MobF32C>(a, slot_node, nslots, anti, num_sms, st, launches);
+    }
+}
+
+}  // namespace mz
