@@ -86,7 +86,13 @@ typedef struct {
     int32_t build_transpose;  /* nonzero: also build the dual poset's plan for mz_zeta_T / mz_mobius_T */
     int32_t host_only;        /* nonzero: build host structures only (no device use at all) */
     int32_t mobius_schedule;  /* an mz_schedule value */
-    int32_t reserved0;
+    int32_t mobius_blocks_per_sm; /* resident 128-thread blocks per SM of the Moebius forward
+                                     substitution (one thread per row); 0 = default (2) */
+    int32_t mobius_pace_ns;   /* Moebius forward substitution: before polling for a row that is
+                                 d levels above the row it just finished, a thread sleeps about
+                                 (d - 2) * pace ns, so rows far from the frontier do not load L2
+                                 with polls. 0 = default (1000); negative = no pacing */
+    int32_t reserved1;
     int64_t spin_limit;       /* bound on polling iterations of every device-side wait; 0 = default (2^22) */
     /* Test hook, 0 = off. v > 0 makes every transform of this plan skip one publication:
        the look-back flag of scan tile v-1 and the y' word of the (v-1)-th row of the

@@ -46,7 +46,8 @@ class MzError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("build_transpose", ctypes.c_int32), ("host_only", ctypes.c_int32),
-                ("mobius_schedule", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("mobius_schedule", ctypes.c_int32), ("mobius_blocks_per_sm", ctypes.c_int32),
+                ("mobius_pace_ns", ctypes.c_int32), ("reserved1", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("debug_withhold", ctypes.c_int64),
                 ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
 
@@ -105,13 +106,14 @@ def _check(st: int, where: str):
 # ----------------------------------------------------------------------------- C entry points
 
 def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, host_only: bool = False,
-             mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0) -> int:
+             mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0,
+             mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0) -> int:
     """mz_build: returns the plan handle (an integer). Host arrays are int32."""
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
     cid = None if chain_id is None else np.ascontiguousarray(chain_id, dtype=np.int32)
-    opts = _Opts(int(build_transpose), int(host_only), int(mobius_schedule), 0, int(spin_limit),
-                 int(debug_withhold), None, None, None)
+    opts = _Opts(int(build_transpose), int(host_only), int(mobius_schedule), int(mobius_blocks_per_sm),
+                 int(mobius_pace_ns), 0, int(spin_limit), int(debug_withhold), None, None, None)
     out = ctypes.c_void_p()
     st = lib.mz_build(int(n), int(src.size), src.ctypes.data, dst.ctypes.data,
                       None if cid is None else cid.ctypes.data, ctypes.byref(opts), ctypes.byref(out))

@@ -78,7 +78,10 @@ static mz_status upload_side(mz_plan *p, int side) {
     const HostSide &H = p->host[side];
     DeviceSide &D = p->dev[side];
     const int64_t n = H.n, k = H.k;
-    mz_status st = upload(p, &D.slot_node, H.slot_node.data(), (size_t)(n + k));
+    // padded with -1 to a multiple of 64 entries: the scan reads it as 16-byte vectors
+    std::vector<int32_t> sn(H.slot_node);
+    sn.resize(((size_t)(n + k) + 63) / 64 * 64, -1);
+    mz_status st = upload(p, &D.slot_node, sn.data(), sn.size());
     if (st) return st;
     D.ntiles = (n + kTileRows - 1) / kTileRows;
     {
@@ -109,25 +112,41 @@ static mz_status upload_side(mz_plan *p, int side) {
         for (int64_t r = 0; r < n; ++r) order[r] = r;
         std::stable_sort(order.begin(), order.end(),
                          [&](int64_t a, int64_t b) { return lvl[H.row_node[a]] < lvl[H.row_node[b]]; });
-        std::vector<int32_t> Nm, mnode(n), mslot(n);
+        std::vector<int32_t> Nm, mnode(n), mslot(n), mlevel(n);
+        const int64_t kp = (k + 15) / 16 * 16;   // rows padded with slot 0 (a zero slot) in front
+        D.kpad = (int32_t)kp;
         try {
-            Nm.resize((size_t)n * k);
+            Nm.assign((size_t)n * kp, 0);
         } catch (...) {
             set_last_error("host allocation failed");
             return MZ_ERR_OOM;
         }
+        // Each row lists its k slots ordered by the level of the element in them
+        // (zero slots first): the kernel adds the latest-finishing ones last.
+        std::vector<std::pair<int32_t, int32_t>> cols(k);
         for (int64_t i = 0; i < n; ++i) {
             const int64_t r = order[i];
             const int32_t x = H.row_node[r];
             const int32_t cx = H.chain_id[x];
-            std::memcpy(&Nm[(size_t)i * k], &H.N[(size_t)r * k], sizeof(int32_t) * k);
-            Nm[(size_t)i * k + cx] = (int32_t)H.chain_base[cx];   // own chain: handled apart
+            const int32_t *src = &H.N[(size_t)r * k];
+            for (int64_t c = 0; c < k; ++c) {
+                const int32_t slot = (c == cx) ? (int32_t)H.chain_base[cx] : src[c];   // own chain: handled apart
+                const int32_t y = H.slot_node[slot];
+                cols[c] = {y < 0 ? -1 : lvl[y], slot};
+            }
+            std::stable_sort(cols.begin(), cols.end(),
+                             [](const std::pair<int32_t, int32_t> &a, const std::pair<int32_t, int32_t> &b) {
+                                 return a.first < b.first;
+                             });
+            for (int64_t c = 0; c < k; ++c) Nm[(size_t)i * kp + (kp - k) + c] = cols[c].second;
             mnode[i] = x;
             mslot[i] = H.node_slot[x];
+            mlevel[i] = lvl[x];
         }
         if ((st = upload(p, &D.Nm, Nm.data(), Nm.size()))) return st;
         if ((st = upload(p, &D.mob_node, mnode.data(), mnode.size()))) return st;
         if ((st = upload(p, &D.mob_slot, mslot.data(), mslot.size()))) return st;
+        if ((st = upload(p, &D.mob_level, mlevel.data(), mlevel.size()))) return st;
     }
     return MZ_OK;
 }
@@ -256,10 +275,14 @@ static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const vo
     const DeviceSide &D = p->dev[side];
     MobArgs ma;
     ma.Nm = D.Nm;
+    ma.kpad = D.kpad;
+    ma.blocks_per_sm = p->mob_blocks_per_sm;
     ma.mob_node = D.mob_node;
     ma.mob_slot = D.mob_slot;
+    ma.mob_level = D.mob_level;
+    ma.pace_ns = p->mob_pace_ns;
     ma.n = H.n;
-    ma.k = H.k;
+    ma.k = D.kpad;   // the Moebius kernels walk whole padded rows
     ma.B = B;
     ma.g = g;
     ma.f = f;
@@ -327,6 +350,8 @@ mz_status mz_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     p->schedule = o.mobius_schedule;
     p->host_only = o.host_only != 0;
     if (o.spin_limit > 0) p->spin_limit = o.spin_limit;
+    if (o.mobius_blocks_per_sm > 0) p->mob_blocks_per_sm = o.mobius_blocks_per_sm;
+    if (o.mobius_pace_ns != 0) p->mob_pace_ns = o.mobius_pace_ns < 0 ? 0 : o.mobius_pace_ns;
     p->withhold = o.debug_withhold > 0 ? o.debug_withhold - 1 : -1;
     p->dev_alloc = o.dev_alloc;
     p->dev_free = o.dev_free;

@@ -47,7 +47,9 @@ struct DeviceSide {
     int32_t *Nm = nullptr;         // [n][k] rows in Moebius processing order; own column -> zero slot
     int32_t *mob_node = nullptr;   // [n] node of the i-th processed row
     int32_t *mob_slot = nullptr;   // [n] its slot
+    int32_t *mob_level = nullptr;  // [n] its level in the schedule
     int64_t ntiles = 0;
+    int32_t kpad = 0;              // Moebius row length (k rounded up to 16)
 };
 
 }  // namespace mz
@@ -63,6 +65,8 @@ struct mz_plan {
     uint32_t *d_status = nullptr;   // device status word (MZ_OK / MZ_ERR_TIMEOUT)
     int device = -1;
     int num_sms = 0;
+    int32_t mob_blocks_per_sm = 2;  // one-thread-per-row wavefront: blocks of 128 threads per SM
+    int32_t mob_pace_ns = 1000;     // wavefront pacing per level of distance (0: none)
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
     void *(*dev_alloc)(size_t, void *) = nullptr;

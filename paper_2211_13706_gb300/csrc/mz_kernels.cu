@@ -81,7 +81,38 @@ __device__ __forceinline__ unsigned long long wait_value(const unsigned long lon
             report(status, MZ_ERR_TIMEOUT);
             return 0;
         }
-        if (it > 64) __nanosleep(64);
+        if (it > 256) __nanosleep(32);
+    }
+}
+
+// Wait until none of the NV words v[j] (read from P[idx[j]], idx[j] >= 0) is the
+// sentinel. Every round re-issues all missing loads together, so a lane pays
+// about one round trip after its last value lands, whatever the number missing.
+template <int NV>
+__device__ __forceinline__ void wait_values(unsigned long long *v, const int32_t *idx, const unsigned long long *P,
+                                            unsigned long long sentinel, uint32_t *status, int64_t limit) {
+    for (int64_t it = 0;; ++it) {
+        bool missing = false;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) missing |= (idx[j] >= 0 && v[j] == sentinel);
+        if (!missing) return;
+        if ((it & 255) == 255 && ld_relaxed_u32(status)) {
+#pragma unroll
+            for (int j = 0; j < NV; ++j)
+                if (v[j] == sentinel) v[j] = 0ull;
+            return;
+        }
+        if (it >= limit) {
+            report(status, MZ_ERR_TIMEOUT);
+#pragma unroll
+            for (int j = 0; j < NV; ++j)
+                if (v[j] == sentinel) v[j] = 0ull;
+            return;
+        }
+        if (it > 256) __nanosleep(32);
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+            if (idx[j] >= 0 && v[j] == sentinel) v[j] = ld_relaxed_u64(P + idx[j]);
     }
 }
 
@@ -113,19 +144,33 @@ __global__ void __launch_bounds__(kScanThreads) k_chain_scan(ScanArgs a) {
     const bool colok = active && b < a.B;
     const int64_t slot0 = tile * (int64_t)R * kScanSeg + (int64_t)r * kScanSeg;
 
+    // all loads first (slot map as 16-byte vectors, then the f gathers), arithmetic after
+    int32_t sn[kScanSeg];
+    if (colok && slot0 < a.nslots) {
+        const int4 *sv = reinterpret_cast<const int4 *>(a.slot_node + slot0);   // padded to 64 entries
+#pragma unroll
+        for (int q = 0; q < kScanSeg / 4; ++q) {
+            const int4 w = sv[q];
+            sn[4 * q] = w.x; sn[4 * q + 1] = w.y; sn[4 * q + 2] = w.z; sn[4 * q + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanSeg; ++j) sn[j] = -1;
+    }
     P_t vals[kScanSeg];
+#pragma unroll
+    for (int j = 0; j < kScanSeg; ++j)
+        vals[j] = (sn[j] >= 0 && slot0 + j < a.nslots) ? Pol::load_in(a.f, (int64_t)sn[j] * a.B + b, a.nB) : Pol::zero();
     P_t acc = Pol::zero();
     int first_reset = kScanSeg;
 #pragma unroll
     for (int j = 0; j < kScanSeg; ++j) {
-        const int64_t s = slot0 + j;
-        if (colok && s < a.nslots) {
-            const int32_t node = a.slot_node[s];
-            if (node < 0) {                        // zero slot: a chain starts here
+        if (colok && slot0 + j < a.nslots) {
+            if (sn[j] < 0) {                       // zero slot: a chain starts here
                 acc = Pol::zero();
                 if (first_reset == kScanSeg) first_reset = j;
             } else {
-                acc = Pol::scan_add(acc, Pol::load_in(a.f, (int64_t)node * a.B + b, a.nB));
+                acc = Pol::scan_add(acc, vals[j]);
             }
         }
         vals[j] = acc;
@@ -275,6 +320,303 @@ __device__ __forceinline__ T shfl_xor_t(T v, int off) {
     return __shfl_xor_sync(0xffffffffu, v, off);
 }
 
+// One warp per row, B == 1. The host orders every row of the map by the level
+// of the dependency (earliest first), so the last kLate columns hold the
+// dependencies that finish last. Lanes sum the early columns (usually ready at
+// once) and reduce them into lane 0 while lane 0 waits for the late ones; after
+// the last dependency lands only a few additions stand between it and the
+// store. The next row of the warp (map entries, node, slot) is loaded while the
+// current one waits, and its g value right after the current store.
+constexpr int kLate = 8;
+
+template <class M, bool ANTI, int KMAX>
+__device__ __forceinline__ void wave_b1(const MobArgs &a, int64_t warp, int64_t nwarps, int lane) {
+    using T = typename M::T;
+    const int k = a.k;
+    const int kearly = k > kLate ? k - kLate : 0;
+    unsigned long long *P = a.P;
+    const unsigned long long SENT = M::kSentinel;
+    int32_t idx[KMAX], nidx[KMAX], late[kLate], nlate[kLate];
+    int64_t i = warp;
+    if (i >= a.n) return;
+    auto load_row = [&](int64_t r, int32_t *out, int32_t *lt) {
+        const int32_t *row = a.Nm + r * (int64_t)k;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            const int c = lane + 32 * j;
+            out[j] = c < kearly ? __ldcs(row + c) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < kLate; ++j) lt[j] = (lane == 0 && kearly + j < k) ? __ldcs(row + kearly + j) : -1;
+    };
+    load_row(i, idx, late);
+    int64_t node = a.mob_node[i], sout = a.mob_slot[i];
+    T gx = lane == 0 ? M::load_in(a.g, node, a.nB) : T(0);
+    for (; i < a.n; i += nwarps) {
+        unsigned long long v[KMAX], lv[kLate];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) v[j] = idx[j] >= 0 ? ld_relaxed_u64(P + idx[j]) : 0ull;
+#pragma unroll
+        for (int j = 0; j < kLate; ++j) lv[j] = late[j] >= 0 ? ld_relaxed_u64(P + late[j]) : 0ull;
+        unsigned long long vprev = 0;
+        if (ANTI && lane == 0) vprev = ld_relaxed_u64(P + sout - 1);
+        const int64_t inext = i + nwarps;
+        int64_t nnode = 0, nsout = 0;
+        if (inext < a.n) {
+            load_row(inext, nidx, nlate);
+            nnode = a.mob_node[inext];
+            nsout = a.mob_slot[inext];
+        }
+        // early columns: every lane, then a reduction into lane 0
+        wait_values<KMAX>(v, idx, P, SENT, a.status, a.spin_limit);
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+            if (idx[j] >= 0) acc = M::add(acc, M::from_bits(v[j]));
+        // late values still missing: ask again now, so the answers arrive during the reduction
+#pragma unroll
+        for (int j = 0; j < kLate; ++j)
+            if (late[j] >= 0 && lv[j] == SENT) lv[j] = ld_relaxed_u64(P + late[j]);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) acc = M::add(acc, __shfl_down_sync(0xffffffffu, acc, off));
+        if (lane == 0) {
+            // late columns, latest last
+            wait_values<kLate>(lv, late, P, SENT, a.status, a.spin_limit);
+#pragma unroll
+            for (int j = 0; j < kLate; ++j)
+                if (late[j] >= 0) acc = M::add(acc, M::from_bits(lv[j]));
+            const bool publish = (i != a.withhold);
+            if (ANTI) {
+                if (vprev == SENT) vprev = wait_value(P + sout - 1, SENT, a.status, a.spin_limit);
+                const T prev = M::from_bits(vprev);
+                const T fx = M::sub(gx, M::add(acc, prev));
+                if (publish) st_relaxed_u64(P + sout, M::to_bits(M::add(prev, fx)));
+                M::store_out(a.f, node, a.nB, fx);
+            } else if (publish) {
+                st_relaxed_u64(P + sout, M::to_bits(M::sub(gx, acc)));
+            }
+            if (inext < a.n) gx = M::load_in(a.g, nnode, a.nB);
+        }
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) idx[j] = nidx[j];
+#pragma unroll
+        for (int j = 0; j < kLate; ++j) late[j] = nlate[j];
+        node = nnode;
+        sout = nsout;
+    }
+}
+
+// Waits, in column order, for each word that still holds the sentinel: polls the
+// first missing one, and once it lands asks again for every later missing one
+// in a single round. Columns are sorted by dependency level, so words tend to
+// land in order; a thread sends one request per round instead of one per word.
+template <int NV>
+__device__ __forceinline__ void wait_in_order(unsigned long long *v, const int32_t *id, const unsigned long long *P,
+                                              unsigned long long sentinel, uint32_t *status, int64_t limit) {
+    // bit j of `miss` set while v[j] holds the sentinel; all indexing stays static
+    uint32_t miss = 0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) miss |= (v[j] == sentinel ? 1u : 0u) << j;
+    for (int64_t it = 0; miss; ++it) {
+        const int first = __ffs(miss) - 1;
+        bool landed = false;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            if (j == first) {
+                v[j] = ld_relaxed_u64(P + id[j]);
+                landed = v[j] != sentinel;
+            }
+        }
+        if (landed) {   // ask again, in one round, for every later word still missing
+#pragma unroll
+            for (int j = 0; j < NV; ++j)
+                if (j > first && ((miss >> j) & 1u)) v[j] = ld_relaxed_u64(P + id[j]);
+        }
+        miss = 0;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) miss |= (v[j] == sentinel ? 1u : 0u) << j;
+        if (!miss) return;
+        if (((it & 255) == 255 && ld_relaxed_u32(status)) || it >= limit) {
+            if (it >= limit) report(status, MZ_ERR_TIMEOUT);
+#pragma unroll
+            for (int j = 0; j < NV; ++j)
+                if (v[j] == sentinel) v[j] = 0ull;
+            return;
+        }
+        if (!landed && it > 128) __nanosleep(64);
+    }
+}
+
+// Sums the NV words v[j] = P[id[j]] into acc in column order, adding each one as
+// soon as it and all before it are present: columns are sorted by dependency
+// level, so words land roughly in order and when the last one lands only one
+// addition is left. The first missing word is polled with two loads in flight;
+// once it lands every later missing word is requested again in one round.
+template <class M, int NV>
+__device__ __forceinline__ void sum_in_order(unsigned long long *v, const int32_t *id, const unsigned long long *P,
+                                             typename M::T &acc, uint32_t *status, int64_t limit) {
+    const unsigned long long S = M::kSentinel;
+    int next = 0;
+    auto advance = [&]() {
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+            if (j == next && v[j] != S) {
+                acc = M::add(acc, M::from_bits(v[j]));
+                next = j + 1;
+            }
+    };
+    advance();
+    for (int64_t it = 0; next < NV; ++it) {
+        const unsigned long long *addr = P;
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+            if (j == next) addr = P + id[j];
+        const unsigned long long a0 = ld_relaxed_u64(addr);
+        __nanosleep(32);
+        const unsigned long long a1 = ld_relaxed_u64(addr);
+        const unsigned long long got = a0 != S ? a0 : a1;
+        if (got != S) {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                if (j == next) v[j] = got;
+                else if (j > next && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
+            }
+        } else if ((it & 127) == 127 && (ld_relaxed_u32(status) || it >= limit)) {
+            if (it >= limit) report(status, MZ_ERR_TIMEOUT);
+#pragma unroll
+            for (int j = 0; j < NV; ++j)
+                if (v[j] == S) v[j] = 0ull;
+        }
+        advance();
+    }
+}
+
+// One thread per row, B == 1. Rows have kpad columns (a multiple of 16; the
+// padding entries come first and point at slot 0, a zero slot), sorted by the
+// level of their dependency, so the last chunk of 16 holds the ones that finish
+// last. A thread never waits for another thread's columns: once its last
+// dependency lands, one poll round, a few additions and the store remain.
+// The ids of the next chunk load while the current chunk is awaited, and the
+// thread's next row is prefetched into L1 at the start of each row.
+constexpr int kChunk = 16;
+
+__device__ __forceinline__ void load_ids(const int32_t *p, int32_t *id) {
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+#pragma unroll
+    for (int t = 0; t < kChunk / 4; ++t) {
+        const int4 w = __ldg(q + t);
+        id[4 * t] = w.x; id[4 * t + 1] = w.y; id[4 * t + 2] = w.z; id[4 * t + 3] = w.w;
+    }
+}
+
+template <class M, bool ANTI>
+__global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
+    using T = typename M::T;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int kp = a.kpad;
+    unsigned long long *P = a.P;
+    const unsigned long long SENT = M::kSentinel;
+    int32_t done_level = 0;   // level of the row this thread finished last (the frontier was there)
+    for (int64_t i = tid; i < a.n; i += nthreads) {
+        const int32_t *row = a.Nm + i * (int64_t)kp;
+        const int32_t level = a.mob_level[i];
+        // The dependencies of this row sit at least one level lower; levels finish one
+        // after the other, so sleep through the ones that must come first.
+        if (a.pace_ns > 0) {
+            int64_t ns = (int64_t)(level - done_level - 2) * a.pace_ns;
+            while (ns > 0) {
+                const unsigned q = ns > 500000 ? 500000u : (unsigned)ns;
+                __nanosleep(q);
+                ns -= q;
+            }
+        }
+        if (i + nthreads < a.n) {
+            const char *nxt = reinterpret_cast<const char *>(row + nthreads * (int64_t)kp);
+            for (int b = 0; b < kp * 4; b += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + b));
+        }
+        const int64_t node = a.mob_node[i];
+        const int64_t sout = a.mob_slot[i];
+        const T gx = M::load_in(a.g, node, a.nB);
+        unsigned long long vprev = ANTI ? ld_relaxed_u64(P + sout - 1) : 0ull;
+        int32_t id[kChunk], nid[kChunk];
+        load_ids(row, id);
+        T acc = T(0);
+        // all chunks but the last: in column order
+        for (int c0 = 0; c0 + kChunk < kp; c0 += kChunk) {
+            unsigned long long v[kChunk];
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(P + id[j]);
+            load_ids(row + c0 + kChunk, nid);
+            sum_in_order<M, kChunk>(v, id, P, acc, a.status, a.spin_limit);
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) id[j] = nid[j];
+        }
+        // The last chunk holds the latest dependencies. The row is finished and
+        // published inside the waiting loop itself, the moment its last value is
+        // in: a lane never waits for the other lanes of its warp to publish.
+        {
+            const unsigned long long S = SENT;
+            unsigned long long v[kChunk];
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(P + id[j]);
+            int next = 0;
+            const bool publish = (i != a.withhold);
+            for (int64_t it = 0;; ++it) {
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j)
+                    if (j == next && v[j] != S) {
+                        acc = M::add(acc, M::from_bits(v[j]));
+                        next = j + 1;
+                    }
+                if (ANTI && next == kChunk && vprev == S) vprev = ld_relaxed_u64(P + sout - 1);
+                if (next == kChunk && (!ANTI || vprev != S)) {
+                    if (ANTI) {
+                        const T prev = M::from_bits(vprev);
+                        const T fx = M::sub(gx, M::add(acc, prev));
+                        if (publish) st_relaxed_u64(P + sout, M::to_bits(M::add(prev, fx)));
+                        M::store_out(a.f, node, a.nB, fx);
+                    } else if (publish) {
+                        st_relaxed_u64(P + sout, M::to_bits(M::sub(gx, acc)));
+                    }
+                    break;
+                }
+                if ((it & 127) == 127 && (ld_relaxed_u32(a.status) || it >= a.spin_limit)) {
+                    if (it >= a.spin_limit) report(a.status, MZ_ERR_TIMEOUT);
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        if (v[j] == S) v[j] = 0ull;
+                    if (vprev == S) vprev = 0ull;
+                    continue;
+                }
+                if (next < kChunk) {
+                    const unsigned long long *addr = P;
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        if (j == next) addr = P + id[j];
+                    const unsigned long long got = ld_relaxed_u64(addr);
+                    if (got != S) {
+#pragma unroll
+                        for (int j = 0; j < kChunk; ++j) {
+                            if (j == next) v[j] = got;
+                            else if (j > next && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
+                        }
+                    }
+                }
+            }
+        }
+        done_level = level;
+    }
+}
+
+template <class M, bool ANTI, int KMAX>
+__global__ void __launch_bounds__(256) k_mob_wave_b1(MobArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    wave_b1<M, ANTI, KMAX>(a, warp, nwarps, lane);
+}
+
 template <class M, bool ANTI>
 __global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
     using T = typename M::T;
@@ -418,16 +760,31 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     if (e != cudaSuccess) return e;
     mark_event(++*launches, st);
     // persistent wavefront: every block resident (cooperative launch), one warp per row
-    void *fn = anti ? (void *)k_mob_wave<M, true> : (void *)k_mob_wave<M, false>;
+    void *fn;
+    int threads = 256;
+    const bool per_thread = a.B == 1;
+    if (per_thread) {
+        threads = 128;
+        fn = anti ? (void *)k_mob_wave_t<M, true> : (void *)k_mob_wave_t<M, false>;
+    } else if (a.B == 1 && a.k <= 256 + kLate) {
+        fn = anti ? (void *)k_mob_wave_b1<M, true, 8> : (void *)k_mob_wave_b1<M, false, 8>;
+    } else {
+        fn = anti ? (void *)k_mob_wave<M, true> : (void *)k_mob_wave<M, false>;
+    }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
     if (e != cudaSuccess) return e;
+    // One thread per row: enough resident threads for several levels of rows in
+    // flight, few enough that the threads waiting ahead of the frontier do not
+    // flood L2 with polls.
     int64_t blocks = (int64_t)std::max(1, per_sm) * num_sms;
-    blocks = std::min<int64_t>(blocks, (a.n + 7) / 8);
+    if (per_thread) blocks = std::min<int64_t>(blocks, (int64_t)std::max(1, a.blocks_per_sm) * num_sms);
+    const int64_t rows_per_block = per_thread ? threads : threads / 32;
+    blocks = std::min<int64_t>(blocks, (a.n + rows_per_block - 1) / rows_per_block);
     blocks = std::max<int64_t>(blocks, 1);
     MobArgs args = a;
     void *params[] = {&args};
-    e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(256), params, 0, st);
+    e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(threads), params, 0, st);
     if (e != cudaSuccess) return e;
     mark_event(++*launches, st);
     if (!anti) {

@@ -44,9 +44,13 @@ struct GatherArgs {
 };
 
 struct MobArgs {
-    const int32_t *Nm;
+    const int32_t *Nm;       // [n][kpad] rows in processing order
+    int32_t kpad;            // row length: k rounded up to a multiple of 16
+    int32_t blocks_per_sm;   // one-thread-per-row kernel: resident blocks of 128 per SM
     const int32_t *mob_node;
     const int32_t *mob_slot;
+    const int32_t *mob_level;   // level of each processed row
+    int32_t pace_ns;            // sleep per level of distance before polling (0: none)
     int64_t n;
     int32_t k, B;
     const void *g;
