@@ -447,12 +447,12 @@ __device__ __forceinline__ void wait_in_order(unsigned long long *v, const int32
     }
 }
 
-// Sums the NV words v[j] = P[id[j]] into acc in column order, adding each one as
+// Sums the NV words v[j] = P[id[j]] into acc (or subtracts them, SUB) in column order, adding each one as
 // soon as it and all before it are present: columns are sorted by dependency
 // level, so words land roughly in order and when the last one lands only one
 // addition is left. The first missing word is polled with two loads in flight;
 // once it lands every later missing word is requested again in one round.
-template <class M, int NV>
+template <class M, int NV, bool SUB>
 __device__ __forceinline__ void sum_in_order(unsigned long long *v, const int32_t *id, const unsigned long long *P,
                                              typename M::T &acc, uint32_t *status, int64_t limit) {
     const unsigned long long S = M::kSentinel;
@@ -461,7 +461,7 @@ __device__ __forceinline__ void sum_in_order(unsigned long long *v, const int32_
 #pragma unroll
         for (int j = 0; j < NV; ++j)
             if (j == next && v[j] != S) {
-                acc = M::add(acc, M::from_bits(v[j]));
+                acc = SUB ? M::sub(acc, M::from_bits(v[j])) : M::add(acc, M::from_bits(v[j]));
                 next = j + 1;
             }
     };
@@ -541,14 +541,17 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
         unsigned long long vprev = ANTI ? ld_relaxed_u64(P + sout - 1) : 0ull;
         int32_t id[kChunk], nid[kChunk];
         load_ids(row, id);
-        T acc = T(0);
+        // U form: acc runs as g(x) - (sum of the values so far), so that once the last
+        // value lands one subtraction is left; the antichain form sums, as it needs
+        // y'(next(x)) apart.
+        T acc = ANTI ? T(0) : gx;
         // all chunks but the last: in column order
         for (int c0 = 0; c0 + kChunk < kp; c0 += kChunk) {
             unsigned long long v[kChunk];
 #pragma unroll
             for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(P + id[j]);
             load_ids(row + c0 + kChunk, nid);
-            sum_in_order<M, kChunk>(v, id, P, acc, a.status, a.spin_limit);
+            sum_in_order<M, kChunk, !ANTI>(v, id, P, acc, a.status, a.spin_limit);
 #pragma unroll
             for (int j = 0; j < kChunk; ++j) id[j] = nid[j];
         }
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j)
                     if (j == next && v[j] != S) {
-                        acc = M::add(acc, M::from_bits(v[j]));
+                        acc = ANTI ? M::add(acc, M::from_bits(v[j])) : M::sub(acc, M::from_bits(v[j]));
                         next = j + 1;
                     }
                 if (ANTI && next == kChunk && vprev == S) vprev = ld_relaxed_u64(P + sout - 1);
@@ -577,7 +580,7 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
                         if (publish) st_relaxed_u64(P + sout, M::to_bits(M::add(prev, fx)));
                         M::store_out(a.f, node, a.nB, fx);
                     } else if (publish) {
-                        st_relaxed_u64(P + sout, M::to_bits(M::sub(gx, acc)));
+                        st_relaxed_u64(P + sout, M::to_bits(acc));
                     }
                     break;
                 }
@@ -589,20 +592,10 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
                     if (vprev == S) vprev = 0ull;
                     continue;
                 }
-                if (next < kChunk) {
-                    const unsigned long long *addr = P;
+                // one round: ask again for every missing word at once
 #pragma unroll
-                    for (int j = 0; j < kChunk; ++j)
-                        if (j == next) addr = P + id[j];
-                    const unsigned long long got = ld_relaxed_u64(addr);
-                    if (got != S) {
-#pragma unroll
-                        for (int j = 0; j < kChunk; ++j) {
-                            if (j == next) v[j] = got;
-                            else if (j > next && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
-                        }
-                    }
-                }
+                for (int j = 0; j < kChunk; ++j)
+                    if (j >= next && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
             }
         }
         done_level = level;
