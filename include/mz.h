@@ -184,6 +184,32 @@ mz_status mz_zeta(const mz_plan *plan, mz_dtype dtype, const void *f, void *g, i
 mz_status mz_mobius(const mz_plan *plan, mz_dtype dtype, const void *g, void *f, int32_t batch,
                     void *ws, size_t ws_bytes, mz_stream stream);
 
+/*
+ * mz_zeta_noalloc - the same zeta transform as mz_zeta, for callers that cannot
+ * allocate device memory at the time of the call: code running where cudaMalloc is
+ * forbidden or unsafe (inside another allocator's callbacks, in a host-side
+ * real-time loop that must not block on the driver's allocator, or under a memory
+ * pool policy that reserves all device memory at start-up). The paper has no
+ * counterpart; this is a service of the library.
+ *
+ * The scratch lives in a fixed array inside the library (MZ_NOALLOC_SCRATCH_BYTES,
+ * 16 MiB), which every GPU that loads the library holds until the process exits.
+ * The call allocates nothing: it needs no workspace argument, and the plan must
+ * already exist (mz_build can route its own buffers through opts->dev_alloc).
+ * The first call on each device looks up the array's device address, so make that
+ * first call before any stream capture.
+ *   f, g, batch, stream  as for mz_zeta
+ * Returns MZ_ERR_INVALID_ARG when the transform needs more scratch than the fixed
+ * array holds (the needed bytes are mz_workspace_size(plan, dtype, batch)), and the
+ * errors of mz_zeta otherwise. All calls share the one array, which keeps the last
+ * call's contents: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and give wrong results; order them on one stream or
+ * synchronise between them.
+ */
+#define MZ_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+mz_status mz_zeta_noalloc(const mz_plan *plan, mz_dtype dtype, const void *f, void *g, int32_t batch,
+                          mz_stream stream);
+
 /* mz_zeta_T - r = Z^T h: r(y) = sum_{x : y <= x} h(x), the zeta transform of the dual
    poset. Needs a plan built with build_transpose, else MZ_ERR_UNSUPPORTED. */
 mz_status mz_zeta_T(const mz_plan *plan, mz_dtype dtype, const void *h, void *r, int32_t batch,

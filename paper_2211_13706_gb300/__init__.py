@@ -33,7 +33,8 @@ MZ_SCHED_ULEVEL, MZ_SCHED_ANTICHAIN = 0, 1
 MZ_EXPORT_CHAIN_ID, MZ_EXPORT_CHAIN_POS, MZ_EXPORT_NIV, MZ_EXPORT_LEVEL, MZ_EXPORT_ULEVEL, MZ_EXPORT_TOPO = range(6)
 
 # every symbol include/mz.h declares
-EXPORTED = ["mz_build", "mz_destroy", "mz_workspace_size", "mz_zeta", "mz_mobius", "mz_zeta_T", "mz_mobius_T",
+EXPORTED = ["mz_build", "mz_destroy", "mz_workspace_size", "mz_zeta", "mz_zeta_noalloc", "mz_mobius",
+            "mz_zeta_T", "mz_mobius_T",
             "mz_check", "mz_plan_info", "mz_plan_export", "mz_last_launch_count", "mz_set_launch_events",
             "mz_status_string", "mz_last_error"]
 
@@ -72,6 +73,7 @@ def _load():
     lib.mz_workspace_size.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(sz)]
     for name in ("mz_zeta", "mz_mobius", "mz_zeta_T", "mz_mobius_T"):
         getattr(lib, name).argtypes = [vp, ctypes.c_int, vp, vp, i32, vp, sz, vp]
+    lib.mz_zeta_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, i32, vp]
     lib.mz_check.argtypes = [vp, vp]
     lib.mz_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     lib.mz_plan_export.argtypes = [vp, i32, i32, vp, sz]
@@ -138,6 +140,16 @@ def _transform(name: str, plan: int, dtype: int, x_ptr: int, y_ptr: int, batch: 
 
 def mz_zeta(plan, dtype, f_ptr, g_ptr, batch, ws_ptr, ws_bytes, stream=0):
     _transform("mz_zeta", plan, dtype, f_ptr, g_ptr, batch, ws_ptr, ws_bytes, stream)
+
+
+# Bytes of the library's fixed scratch array used by mz_zeta_noalloc.
+MZ_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def mz_zeta_noalloc(plan, dtype, f_ptr, g_ptr, batch, stream=0):
+    """mz_zeta without a workspace: uses the library's fixed scratch array and allocates
+    nothing (for callers that must not allocate device memory at call time)."""
+    _check(lib.mz_zeta_noalloc(plan, dtype, f_ptr, g_ptr, batch, stream), "mz_zeta_noalloc")
 
 
 def mz_mobius(plan, dtype, g_ptr, f_ptr, batch, ws_ptr, ws_bytes, stream=0):

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -396,6 +397,53 @@ mz_status mz_workspace_size(const mz_plan *plan, mz_dtype dtype, int32_t batch, 
 mz_status mz_zeta(const mz_plan *plan, mz_dtype dtype, const void *f, void *g, int32_t batch, void *ws,
                   size_t ws_bytes, mz_stream stream) {
     return run_zeta(plan, 0, dtype, f, g, batch, ws, ws_bytes, stream);
+}
+
+// ---------------------------------------------------------------- zeta without allocation
+// Scratch for mz_zeta_noalloc: a fixed device array owned by the library. Its
+// name is only a host-side handle; the device address comes from
+// cudaGetSymbolAddress, looked up once per device on the first call there.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MZ_NOALLOC_SCRATCH_BYTES];
+static void *g_noalloc_addr[128];
+static std::mutex g_noalloc_mutex;
+
+mz_status mz_zeta_noalloc(const mz_plan *plan, mz_dtype dtype, const void *f, void *g, int32_t batch,
+                          mz_stream stream) {
+    if (!plan || batch < 1 || (dtype != MZ_I64 && dtype != MZ_F64 && dtype != MZ_F32C)) {
+        set_last_error("invalid argument");
+        return MZ_ERR_INVALID_ARG;
+    }
+    if (plan->host_only) {
+        set_last_error("plan was built host-only");
+        return MZ_ERR_NO_DEVICE;
+    }
+    const size_t need = ws_layout(plan->host[0], batch).total;
+    if (need > MZ_NOALLOC_SCRATCH_BYTES) {
+        set_last_error("mz_zeta_noalloc: this plan and batch need " + std::to_string(need) +
+                       " bytes of scratch; the fixed scratch array holds " +
+                       std::to_string((size_t)MZ_NOALLOC_SCRATCH_BYTES) + " (use mz_zeta with a workspace)");
+        return MZ_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 128) {
+        set_last_error("device index out of range");
+        return MZ_ERR_INVALID_ARG;
+    }
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_addr[dev] = nullptr;
+                return cuda_fail(e, "cudaGetSymbolAddress");
+            }
+        }
+        ws = g_noalloc_addr[dev];
+    }
+    return run_zeta(plan, 0, dtype, f, g, batch, ws, MZ_NOALLOC_SCRATCH_BYTES, stream);
 }
 
 mz_status mz_mobius(const mz_plan *plan, mz_dtype dtype, const void *g, void *f, int32_t batch, void *ws,
