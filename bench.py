@@ -40,6 +40,8 @@ import numpy as np  # noqa: E402
 import posetgen as pg  # noqa: E402
 
 METRIC = "zeta & Möbius node-values/s, % HBM peak; FP32-compensated vs FP64 plain"
+FP64_ADDS_PER_S = 0.625e12   # GB300 nominal FP64 1.25 TFLOP/s (an FMA counts 2), one add per FMA slot
+HOP_FLOOR_US = 0.45          # SM-to-SM store -> poll latency, measured unloaded on GB300
 UNIT = "node-values/s"
 
 WORKLOADS = {
@@ -332,6 +334,19 @@ def device_arm(args):
     kernels = {name: {"mean_ms": round(v, 5), "share": round(v / sum(kt.values()), 4),
                       "alg_GBps": round(algorithmic_bytes(name, n, k, B) / (v / 1e3) / 1e9, 1)}
                for name, v in kt.items()}
+    # The gather's other roof: one add per gathered term (nnz(N) per launch). In fp64 it is
+    # bound by the FP64 pipe: nominal 1.25 TFLOP/s = 0.625e12 adds/s on GB300.
+    adds = info["nnz"] * B
+    kernels["niv_gather"]["adds_per_s"] = round(adds / (kt["niv_gather"] / 1e3), 1)
+    if args.dtype == "f64":
+        kernels["niv_gather"]["fp64_add_frac_of_nominal"] = round(adds / (kt["niv_gather"] / 1e3) / FP64_ADDS_PER_S, 4)
+    # The forward substitution's roof is latency: U's dependency graph has `ulevels`
+    # levels, and each level costs at least one store-to-poll hop between SMs
+    # (measured unloaded on GB300: about 0.45 us one way).
+    lat_ms = info["ulevels"] * HOP_FLOOR_US / 1e3
+    latency = {"kernel": "mob_wave", "levels": info["ulevels"], "hop_floor_us": HOP_FLOOR_US,
+               "bound_ms": round(lat_ms, 4), "achieved_ms": round(kt["mob_wave"], 4),
+               "frac": round(lat_ms / kt["mob_wave"], 4)}
 
     variants = {}
     if not args.no_variants:
@@ -366,6 +381,7 @@ def device_arm(args):
                    "l2": "flushed between steps (512 MiB write), outside the timed events",
                    "parallelism": f"replicas x{world}", "host_build_s": round(build_s, 2)},
         "roofline": roof,
+        "latency_roof": latency,
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
