@@ -306,6 +306,43 @@ __global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
     }
 }
 
+// Batched gather (B > 1, B a power of two): one warp per tile of 32 rows, G = min(B, 32)
+// lanes per row (lane b0 owns the columns b0 + G t), 32 / G rows at a time. Within a row
+// group the map entry is a broadcast and the G loads of y' are contiguous.
+template <class Pol, int G>
+__global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a) {
+    using P_t = typename Pol::P_t;
+    using Acc = typename Pol::Acc;
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, b0 = lane % G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const P_t *__restrict__ P = reinterpret_cast<const P_t *>(a.P);
+    const int k = a.k;
+    const int64_t B = a.B;
+    for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
+        const int32_t *__restrict__ nt = a.Nt + tile * (int64_t)k * kTileRows;
+        for (int r = sub; r < kTileRows; r += R) {
+            const int32_t node = a.row_node[tile * kTileRows + r];
+            if (node < 0) continue;
+            for (int64_t b = b0; b < B; b += G) {
+                Acc acc = Pol::acc_zero();
+                int c = 0;
+                for (; c + 8 <= k; c += 8) {
+                    int32_t sl[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) sl[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) Pol::acc_add(acc, __ldg(P + (int64_t)sl[u] * B + b));
+                }
+                for (; c < k; ++c) Pol::acc_add(acc, __ldg(P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + r) * B + b));
+                Pol::store_out(a.g, (int64_t)node * B + b, a.nB, acc);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- Moebius
 template <class M>
 __global__ void k_mob_init(const int32_t *__restrict__ slot_node, int64_t nslots, int32_t B,
@@ -509,16 +546,22 @@ __device__ __forceinline__ void load_ids(const int32_t *p, int32_t *id) {
     }
 }
 
-template <class M, bool ANTI>
+// G lanes per row (G = 1 for one function, G = min(B, 32) for B functions, B a
+// power of two): lane b0 of a row group owns the columns b = b0 + G t, t < B / G,
+// and waits only for its own words, so no lane ever waits for another lane.
+template <class M, bool ANTI, int G>
 __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
     using T = typename M::T;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t grp = tid / G, ngrp = nthreads / G;
+    const int b0 = (int)(tid % G);
+    const int64_t B = (G == 1) ? 1 : a.B;
     const int kp = a.kpad;
     unsigned long long *P = a.P;
     const unsigned long long SENT = M::kSentinel;
-    int32_t done_level = 0;   // level of the row this thread finished last (the frontier was there)
-    for (int64_t i = tid; i < a.n; i += nthreads) {
+    int32_t done_level = 0;   // level of the row this group finished last (the frontier was there)
+    for (int64_t i = grp; i < a.n; i += ngrp) {
         const int32_t *row = a.Nm + i * (int64_t)kp;
         const int32_t level = a.mob_level[i];
         // The dependencies of this row sit at least one level lower; levels finish one
@@ -531,71 +574,80 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
                 ns -= q;
             }
         }
-        if (i + nthreads < a.n) {
-            const char *nxt = reinterpret_cast<const char *>(row + nthreads * (int64_t)kp);
-            for (int b = 0; b < kp * 4; b += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + b));
+        if (b0 == 0 && i + ngrp < a.n) {
+            const char *nxt = reinterpret_cast<const char *>(row + ngrp * (int64_t)kp);
+            for (int c = 0; c < kp * 4; c += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + c));
         }
         const int64_t node = a.mob_node[i];
         const int64_t sout = a.mob_slot[i];
-        const T gx = M::load_in(a.g, node, a.nB);
-        unsigned long long vprev = ANTI ? ld_relaxed_u64(P + sout - 1) : 0ull;
-        int32_t id[kChunk], nid[kChunk];
-        load_ids(row, id);
-        // U form: acc runs as g(x) - (sum of the values so far), so that once the last
-        // value lands one subtraction is left; the antichain form sums, as it needs
-        // y'(next(x)) apart.
-        T acc = ANTI ? T(0) : gx;
-        // all chunks but the last: in column order
-        for (int c0 = 0; c0 + kChunk < kp; c0 += kChunk) {
-            unsigned long long v[kChunk];
+        const bool publish = (i != a.withhold);
+        for (int64_t b = b0; b < B; b += G) {
+            unsigned long long *Pb = P + b;           // column b of every slot: Pb[s * B]
+            const T gx = M::load_in(a.g, node * B + b, a.nB);
+            unsigned long long vprev = ANTI ? ld_relaxed_u64(Pb + (sout - 1) * B) : 0ull;
+            int32_t id[kChunk], nid[kChunk];
+            load_ids(row, id);
+            // U form: acc runs as g(x) - (sum of the values so far), so that once the last
+            // value lands one subtraction is left; the antichain form sums, as it needs
+            // y'(next(x)) apart.
+            T acc = ANTI ? T(0) : gx;
+            // all chunks but the last: in column order
+            for (int c0 = 0; c0 + kChunk < kp; c0 += kChunk) {
+                unsigned long long v[kChunk];
+                int32_t sid[kChunk];
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(P + id[j]);
-            load_ids(row + c0 + kChunk, nid);
-            sum_in_order<M, kChunk, !ANTI>(v, id, P, acc, a.status, a.spin_limit);
+                for (int j = 0; j < kChunk; ++j) sid[j] = (int32_t)((int64_t)id[j] * B);
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j) id[j] = nid[j];
-        }
-        // The last chunk holds the latest dependencies. The row is finished and
-        // published inside the waiting loop itself, the moment its last value is
-        // in: a lane never waits for the other lanes of its warp to publish.
-        {
-            const unsigned long long S = SENT;
-            unsigned long long v[kChunk];
+                for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(Pb + sid[j]);
+                load_ids(row + c0 + kChunk, nid);
+                sum_in_order<M, kChunk, !ANTI>(v, sid, Pb, acc, a.status, a.spin_limit);
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(P + id[j]);
-            int next = 0;
-            const bool publish = (i != a.withhold);
-            for (int64_t it = 0;; ++it) {
+                for (int j = 0; j < kChunk; ++j) id[j] = nid[j];
+            }
+            // The last chunk holds the latest dependencies. The row is finished and
+            // published inside the waiting loop itself, the moment its last value is
+            // in: a lane never waits for the other lanes of its warp to publish.
+            {
+                const unsigned long long S = SENT;
+                unsigned long long v[kChunk];
+                int64_t sid[kChunk];
 #pragma unroll
-                for (int j = 0; j < kChunk; ++j)
-                    if (j == next && v[j] != S) {
-                        acc = ANTI ? M::add(acc, M::from_bits(v[j])) : M::sub(acc, M::from_bits(v[j]));
-                        next = j + 1;
-                    }
-                if (ANTI && next == kChunk && vprev == S) vprev = ld_relaxed_u64(P + sout - 1);
-                if (next == kChunk && (!ANTI || vprev != S)) {
-                    if (ANTI) {
-                        const T prev = M::from_bits(vprev);
-                        const T fx = M::sub(gx, M::add(acc, prev));
-                        if (publish) st_relaxed_u64(P + sout, M::to_bits(M::add(prev, fx)));
-                        M::store_out(a.f, node, a.nB, fx);
-                    } else if (publish) {
-                        st_relaxed_u64(P + sout, M::to_bits(acc));
-                    }
-                    break;
-                }
-                if ((it & 127) == 127 && (ld_relaxed_u32(a.status) || it >= a.spin_limit)) {
-                    if (it >= a.spin_limit) report(a.status, MZ_ERR_TIMEOUT);
+                for (int j = 0; j < kChunk; ++j) sid[j] = (int64_t)id[j] * B;
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(Pb + sid[j]);
+                int next = 0;
+                for (int64_t it = 0;; ++it) {
 #pragma unroll
                     for (int j = 0; j < kChunk; ++j)
-                        if (v[j] == S) v[j] = 0ull;
-                    if (vprev == S) vprev = 0ull;
-                    continue;
-                }
-                // one round: ask again for every missing word at once
+                        if (j == next && v[j] != S) {
+                            acc = ANTI ? M::add(acc, M::from_bits(v[j])) : M::sub(acc, M::from_bits(v[j]));
+                            next = j + 1;
+                        }
+                    if (ANTI && next == kChunk && vprev == S) vprev = ld_relaxed_u64(Pb + (sout - 1) * B);
+                    if (next == kChunk && (!ANTI || vprev != S)) {
+                        if (ANTI) {
+                            const T prev = M::from_bits(vprev);
+                            const T fx = M::sub(gx, M::add(acc, prev));
+                            if (publish) st_relaxed_u64(Pb + sout * B, M::to_bits(M::add(prev, fx)));
+                            M::store_out(a.f, node * B + b, a.nB, fx);
+                        } else if (publish) {
+                            st_relaxed_u64(Pb + sout * B, M::to_bits(acc));
+                        }
+                        break;
+                    }
+                    if ((it & 127) == 127 && (ld_relaxed_u32(a.status) || it >= a.spin_limit)) {
+                        if (it >= a.spin_limit) report(a.status, MZ_ERR_TIMEOUT);
 #pragma unroll
-                for (int j = 0; j < kChunk; ++j)
-                    if (j >= next && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
+                        for (int j = 0; j < kChunk; ++j)
+                            if (v[j] == S) v[j] = 0ull;
+                        if (vprev == S) vprev = 0ull;
+                        continue;
+                    }
+                    // one round: ask again for every missing word at once
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        if (j >= next && v[j] == S) v[j] = ld_relaxed_u64(Pb + sid[j]);
+                }
             }
         }
         done_level = level;
@@ -728,6 +780,16 @@ static cudaError_t launch_gather_t(const GatherArgs &a, int num_sms, cudaStream_
     blocks = std::min<int64_t>(blocks, (int64_t)num_sms * 32);
     if (a.B == 1) {
         k_niv_gather<Pol, 1><<<dim3((unsigned)blocks, 1), kGatherThreads, 0, st>>>(a);
+    } else if ((a.B & (a.B - 1)) == 0) {
+        const int G = a.B < 32 ? a.B : 32;
+        const dim3 grid((unsigned)blocks, 1);
+        switch (G) {
+            case 2: k_niv_gather_b<Pol, 2><<<grid, kGatherThreads, 0, st>>>(a); break;
+            case 4: k_niv_gather_b<Pol, 4><<<grid, kGatherThreads, 0, st>>>(a); break;
+            case 8: k_niv_gather_b<Pol, 8><<<grid, kGatherThreads, 0, st>>>(a); break;
+            case 16: k_niv_gather_b<Pol, 16><<<grid, kGatherThreads, 0, st>>>(a); break;
+            default: k_niv_gather_b<Pol, 32><<<grid, kGatherThreads, 0, st>>>(a); break;
+        }
     } else {
         const unsigned gy = (unsigned)((a.B + 3) / 4);
         k_niv_gather<Pol, 4><<<dim3((unsigned)blocks, gy), kGatherThreads, 0, st>>>(a);
@@ -755,10 +817,23 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     // persistent wavefront: every block resident (cooperative launch), one warp per row
     void *fn;
     int threads = 256;
-    const bool per_thread = a.B == 1;
+    // rows per thread group: G = 1 for one function, G = min(B, 32) for a power-of-two batch
+    const bool pow2 = (a.B & (a.B - 1)) == 0;
+    const bool per_thread = pow2 && (int64_t)a.B * (a.n + a.k) < ((int64_t)1 << 31);
+    int G = 1;
     if (per_thread) {
         threads = 128;
-        fn = anti ? (void *)k_mob_wave_t<M, true> : (void *)k_mob_wave_t<M, false>;
+        G = a.B < 32 ? a.B : 32;
+#define MZ_WAVE_G(g) (anti ? (void *)k_mob_wave_t<M, true, g> : (void *)k_mob_wave_t<M, false, g>)
+        switch (G) {
+            case 1: fn = MZ_WAVE_G(1); break;
+            case 2: fn = MZ_WAVE_G(2); break;
+            case 4: fn = MZ_WAVE_G(4); break;
+            case 8: fn = MZ_WAVE_G(8); break;
+            case 16: fn = MZ_WAVE_G(16); break;
+            default: fn = MZ_WAVE_G(32); break;
+        }
+#undef MZ_WAVE_G
     } else if (a.B == 1 && a.k <= 256 + kLate) {
         fn = anti ? (void *)k_mob_wave_b1<M, true, 8> : (void *)k_mob_wave_b1<M, false, 8>;
     } else {
@@ -771,8 +846,8 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     // flight, few enough that the threads waiting ahead of the frontier do not
     // flood L2 with polls.
     int64_t blocks = (int64_t)std::max(1, per_sm) * num_sms;
-    if (per_thread) blocks = std::min<int64_t>(blocks, (int64_t)std::max(1, a.blocks_per_sm) * num_sms);
-    const int64_t rows_per_block = per_thread ? threads : threads / 32;
+    if (per_thread) blocks = std::min<int64_t>(blocks, (int64_t)std::max(1, a.blocks_per_sm) * G * num_sms);
+    const int64_t rows_per_block = per_thread ? threads / G : threads / 32;
     blocks = std::min<int64_t>(blocks, (a.n + rows_per_block - 1) / rows_per_block);
     blocks = std::max<int64_t>(blocks, 1);
     MobArgs args = a;

@@ -140,6 +140,47 @@ def test_c1_float(c1, dtype, sched):
         check_mobius(plan, Z, gin, dtype, f"c1 mobius {kind}", mu=mu)
 
 
+@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("dtype", [mz.MZ_F64, mz.MZ_F32C])
+def test_c1_float_batched(c1, dtype, sched):
+    """Batched floats (B = 4 and 16): every column within tolerance of the oracle."""
+    p, Z, mu = c1
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=sched)
+    for batch in (4, 16):
+        f = values(p.n, batch, dtype, 21, ("f64" if dtype == mz.MZ_F64 else "f32") + "u")
+        got = run(plan, "zeta", f, dtype)
+        for b in range(0, batch, 5):
+            ex = exact_input(f[:, b], dtype)
+            assert_close(got[:, b], oracle.zeta(Z, ex), oracle.zeta(Z, np.abs(from_abs(ex))), dtype,
+                         f"batched zeta B={batch} col {b}")
+    g = values(p.n, 4, dtype, 22, ("f64" if dtype == mz.MZ_F64 else "f32") + "u")
+    gin = g if dtype == mz.MZ_F64 else (g, np.zeros_like(g))
+    out = run(plan, "mobius", gin, dtype)
+    for b in (0, 3):
+        ex = exact_input(g[:, b], dtype)
+        ref = oracle.mobius(Z, ex, "mu", mu=mu)
+        gval = from_abs(ex) if not isinstance(ex, tuple) else ex[0].astype(np.float64)
+        res = oracle.zeta(Z, out[:, b]) - gval
+        assert_close(res, np.zeros_like(res), oracle.zeta(Z, np.abs(out[:, b])) + np.abs(gval), dtype,
+                     f"batched mobius residual col {b}")
+        fwd = np.abs(mu.T).astype(np.float64) @ (Z.astype(np.float64) @ np.abs(ref))
+        assert_close(out[:, b], ref, fwd, dtype, f"batched mobius forward col {b}")
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("batch", [8, 32])
+def test_c1_int64_batched_round_trip_both_schedules(c1, sched, batch):
+    p, Z, mu = c1
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=sched, build_transpose=True)
+    f = values(p.n, batch, mz.MZ_I64, 23)
+    g = run(plan, "zeta", f, mz.MZ_I64)
+    assert (g == (Z.astype(np.int64) @ f)).all()
+    assert (run(plan, "mobius", g, mz.MZ_I64) == f).all()
+    h = run(plan, "zeta_T", f, mz.MZ_I64)
+    assert (h == (Z.T.astype(np.int64) @ f)).all()
+    assert (run(plan, "mobius_T", h, mz.MZ_I64) == f).all()
+
+
 def _split(x):
     hi = x.astype(np.float32)
     lo = (x - hi.astype(np.float64)).astype(np.float32)
