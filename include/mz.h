@@ -118,7 +118,11 @@ typedef struct {
     int32_t ulevels_T;
     int32_t max_chain;     /* longest chain of the decomposition (q in Sec. 4) */
     int64_t device_bytes;  /* device memory held by the plan (dual included) */
+    int32_t components;    /* posets in the plan (1 for mz_build) */
+    int32_t reserved;
 } mz_plan_info_t;
+/* For a plan of several posets (mz_build_batch) n, k, nnz and edges are totals over
+   them and levels, ulevels, levels_T, ulevels_T and max_chain are maxima. */
 
 /* Arrays mz_plan_export can copy out (host memory, no device work). */
 typedef enum {
@@ -151,6 +155,23 @@ typedef enum {
  */
 mz_status mz_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                    const int32_t *chain_id, const mz_build_opts *opts, mz_plan **out);
+
+/*
+ * mz_build_batch - one plan for `count` independent posets, so that one launch of each
+ * kernel transforms all of them (many posets of uneven n and k). The plan is the
+ * plan of their disjoint union: poset p's node x is node off_p + x of the union,
+ * off_p = n[0] + ... + n[p-1], and every transform takes and returns [sum n][batch]
+ * arrays in that order. The zeta and Moebius transforms of a disjoint union act on
+ * each poset separately (no element of one is comparable with an element of another).
+ *   count     number of posets, >= 1; the union may hold at most 2^30 nodes
+ *   n, m      count sizes each; src[p], dst[p] the m[p] edges of poset p (local ids)
+ *   chain_id  NULL, or count pointers, each NULL or n[p] chain ids of poset p
+ *   opts, out as for mz_build
+ * Errors as for mz_build; the message of mz_last_error names the failing poset.
+ */
+mz_status mz_build_batch(int32_t count, const int64_t *n, const int64_t *m, const int32_t *const *src,
+                         const int32_t *const *dst, const int32_t *const *chain_id, const mz_build_opts *opts,
+                         mz_plan **out);
 
 /* Frees the plan and its device buffers (synchronises the device first). NULL is a no-op. */
 void mz_destroy(mz_plan *plan);
@@ -231,7 +252,9 @@ mz_status mz_check(const mz_plan *plan, mz_stream stream);
 mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info);
 
 /* Copies one host-side array of the plan (mz_export) into `out` (`bytes` long).
-   `dual` nonzero selects the dual plan. MZ_ERR_INVALID_ARG if `bytes` is too small. */
+   `dual` nonzero selects the dual plan. MZ_ERR_INVALID_ARG if `bytes` is too small.
+   Plans of several posets export per-node arrays in union order (chain ids and topo
+   entries offset to the union); their niv map is not exported (MZ_ERR_UNSUPPORTED). */
 mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *out, size_t bytes);
 
 /* Kernel launches issued by the last transform call on this thread (memsets excluded). */

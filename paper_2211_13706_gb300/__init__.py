@@ -33,7 +33,7 @@ MZ_SCHED_ULEVEL, MZ_SCHED_ANTICHAIN = 0, 1
 MZ_EXPORT_CHAIN_ID, MZ_EXPORT_CHAIN_POS, MZ_EXPORT_NIV, MZ_EXPORT_LEVEL, MZ_EXPORT_ULEVEL, MZ_EXPORT_TOPO = range(6)
 
 # every symbol include/mz.h declares
-EXPORTED = ["mz_build", "mz_destroy", "mz_workspace_size", "mz_zeta", "mz_zeta_noalloc", "mz_mobius",
+EXPORTED = ["mz_build", "mz_build_batch", "mz_destroy", "mz_workspace_size", "mz_zeta", "mz_zeta_noalloc", "mz_mobius",
             "mz_zeta_T", "mz_mobius_T",
             "mz_check", "mz_plan_info", "mz_plan_export", "mz_last_launch_count", "mz_set_launch_events",
             "mz_status_string", "mz_last_error"]
@@ -57,7 +57,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("has_transpose", ctypes.c_int32),
                 ("nnz", ctypes.c_int64), ("edges", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("ulevels", ctypes.c_int32), ("schedule", ctypes.c_int32), ("levels_T", ctypes.c_int32),
-                ("ulevels_T", ctypes.c_int32), ("max_chain", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("ulevels_T", ctypes.c_int32), ("max_chain", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("components", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -68,6 +69,7 @@ def _load():
     lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
     vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
     lib.mz_build.argtypes = [i64, i64, vp, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
+    lib.mz_build_batch.argtypes = [i32, vp, vp, vp, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
     lib.mz_destroy.argtypes = [vp]
     lib.mz_destroy.restype = None
     lib.mz_workspace_size.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(sz)]
@@ -120,6 +122,27 @@ def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, 
     st = lib.mz_build(int(n), int(src.size), src.ctypes.data, dst.ctypes.data,
                       None if cid is None else cid.ctypes.data, ctypes.byref(opts), ctypes.byref(out))
     _check(st, "mz_build")
+    return out.value
+
+
+def mz_build_batch(posets, *, build_transpose: bool = False, host_only: bool = False,
+                   mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0,
+                   mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0) -> int:
+    """mz_build_batch: `posets` is a list of (n, src, dst, chain_id or None)."""
+    count = len(posets)
+    ns = np.array([int(p[0]) for p in posets], dtype=np.int64)
+    srcs = [np.ascontiguousarray(p[1], dtype=np.int32) for p in posets]
+    dsts = [np.ascontiguousarray(p[2], dtype=np.int32) for p in posets]
+    cids = [None if p[3] is None else np.ascontiguousarray(p[3], dtype=np.int32) for p in posets]
+    ms = np.array([a.size for a in srcs], dtype=np.int64)
+    ptr = lambda arrs: (ctypes.c_void_p * count)(*[None if a is None else a.ctypes.data for a in arrs])
+    psrc, pdst, pcid = ptr(srcs), ptr(dsts), ptr(cids)
+    opts = _Opts(int(build_transpose), int(host_only), int(mobius_schedule), int(mobius_blocks_per_sm),
+                 int(mobius_pace_ns), 0, int(spin_limit), int(debug_withhold), None, None, None)
+    out = ctypes.c_void_p()
+    st = lib.mz_build_batch(count, ns.ctypes.data, ms.ctypes.data, psrc, pdst,
+                            None if all(c is None for c in cids) else pcid, ctypes.byref(opts), ctypes.byref(out))
+    _check(st, "mz_build_batch")
     return out.value
 
 
@@ -216,11 +239,17 @@ def dtype_of(t) -> int:
 class Plan:
     """A built poset plan plus a cached device workspace (allocated through torch)."""
 
-    def __init__(self, n: int, src, dst, chain_id=None, **opts):
-        self.handle = mz_build(n, src, dst, chain_id, **opts)
+    def __init__(self, n: int, src, dst, chain_id=None, *, _handle=None, **opts):
+        self.handle = _handle if _handle is not None else mz_build(n, src, dst, chain_id, **opts)
         self.info = mz_plan_info(self.handle)
         self.n = self.info["n"]
         self._ws = {}
+
+    @classmethod
+    def batch(cls, posets, **opts):
+        """One plan for many posets: a list of (n, src, dst, chain_id or None). Values are
+        [sum n] or [sum n, batch] arrays, poset after poset."""
+        return cls(0, None, None, _handle=mz_build_batch(posets, **opts))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <cstring>
 #include <memory>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <string>
 #include <vector>
@@ -73,78 +75,130 @@ static mz_status upload(mz_plan *p, T **dst, const T *src, size_t count) {
     return MZ_OK;
 }
 
-// Device layouts of one side: the tiled map for the zeta gather and the map in
-// Moebius processing order.
+// Device layouts of one side (all components): the concatenated slot map, the
+// tiled niv map for the zeta gather, and the map in Moebius processing order.
 static mz_status upload_side(mz_plan *p, int side) {
-    const HostSide &H = p->host[side];
+    const std::vector<HostSide> &Hs = p->host[side];
     DeviceSide &D = p->dev[side];
-    const int64_t n = H.n, k = H.k;
-    // padded with -1 to a multiple of 64 entries: the scan reads it as 16-byte vectors
-    std::vector<int32_t> sn(H.slot_node);
-    sn.resize(((size_t)(n + k) + 63) / 64 * 64, -1);
-    mz_status st = upload(p, &D.slot_node, sn.data(), sn.size());
-    if (st) return st;
-    D.ntiles = (n + kTileRows - 1) / kTileRows;
-    {
-        std::vector<int32_t> tiled, rn(D.ntiles * kTileRows, -1);
-        try {
-            tiled.resize((size_t)D.ntiles * k * kTileRows);
-        } catch (...) {
-            set_last_error("host allocation failed");
-            return MZ_ERR_OOM;
-        }
-        for (int64_t r = 0; r < D.ntiles * kTileRows; ++r) {
-            const int64_t tile = r / kTileRows, lane = r % kTileRows;
-            int32_t *dst = &tiled[(size_t)tile * k * kTileRows + lane];
-            if (r < n) {
-                const int32_t *row = &H.N[(size_t)r * k];
-                for (int64_t c = 0; c < k; ++c) dst[c * kTileRows] = row[c];
-                rn[r] = H.row_node[r];
-            } else {
-                for (int64_t c = 0; c < k; ++c) dst[c * kTileRows] = 0;  // slot 0 is a zero slot
+    const size_t C = Hs.size();
+    D.n = p->n_total();
+    D.nslots = p->slots_total();
+    D.k_max = 0;
+    D.kpad_max = 0;
+    for (const HostSide &H : Hs) {
+        D.k_max = std::max(D.k_max, H.k);
+        D.kpad_max = std::max<int32_t>(D.kpad_max, (H.k + 15) / 16 * 16);
+    }
+    mz_status st;
+    {   // slot map, padded with -1 to a multiple of 64 entries (the scan reads 16-byte vectors)
+        std::vector<int32_t> sn(((size_t)D.nslots + 63) / 64 * 64, -1);
+        for (size_t c = 0; c < C; ++c)
+            for (size_t q = 0; q < Hs[c].slot_node.size(); ++q) {
+                const int32_t v = Hs[c].slot_node[q];
+                sn[p->slot_off[c] + q] = v < 0 ? -1 : (int32_t)(v + p->node_off[c]);
+            }
+        if ((st = upload(p, &D.slot_node, sn.data(), sn.size()))) return st;
+    }
+    {   // tiles of 32 rows per component, column-major inside a tile
+        std::vector<int64_t> toff;
+        std::vector<int32_t> tk;
+        size_t total = 0;
+        for (const HostSide &H : Hs) {
+            const int64_t nt = (H.n + kTileRows - 1) / kTileRows;
+            for (int64_t t = 0; t < nt; ++t) {
+                toff.push_back((int64_t)total);
+                tk.push_back(H.k);
+                total += (size_t)H.k * kTileRows;
             }
         }
-        if ((st = upload(p, &D.Nt, tiled.data(), tiled.size()))) return st;
-        if ((st = upload(p, &D.row_node, rn.data(), rn.size()))) return st;
-    }
-    {
-        const std::vector<int32_t> &lvl = (p->schedule == MZ_SCHED_ANTICHAIN) ? H.level : H.ulevel;
-        std::vector<int64_t> order(n);
-        for (int64_t r = 0; r < n; ++r) order[r] = r;
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int64_t a, int64_t b) { return lvl[H.row_node[a]] < lvl[H.row_node[b]]; });
-        std::vector<int32_t> Nm, mnode(n), mslot(n), mlevel(n);
-        const int64_t kp = (k + 15) / 16 * 16;   // rows padded with slot 0 (a zero slot) in front
-        D.kpad = (int32_t)kp;
+        D.ntiles = (int64_t)toff.size();
+        std::vector<int32_t> tiled, rn((size_t)D.ntiles * kTileRows, -1);
         try {
-            Nm.assign((size_t)n * kp, 0);
+            tiled.assign(total, 0);   // padding rows read slot 0, a zero slot
         } catch (...) {
             set_last_error("host allocation failed");
             return MZ_ERR_OOM;
         }
-        // Each row lists its k slots ordered by the level of the element in them
-        // (zero slots first): the kernel adds the latest-finishing ones last.
-        std::vector<std::pair<int32_t, int32_t>> cols(k);
-        for (int64_t i = 0; i < n; ++i) {
-            const int64_t r = order[i];
+        int64_t t0 = 0;
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
+            const int64_t k = H.k, nt = (H.n + kTileRows - 1) / kTileRows;
+            const int32_t so = (int32_t)p->slot_off[c];
+            for (int64_t r = 0; r < H.n; ++r) {
+                const int64_t t = t0 + r / kTileRows, lane = r % kTileRows;
+                int32_t *dst = &tiled[(size_t)toff[t] + lane];
+                const int32_t *row = &H.N[(size_t)r * k];
+                for (int64_t q = 0; q < k; ++q) dst[q * kTileRows] = row[q] + so;
+                rn[(size_t)t * kTileRows + lane] = (int32_t)(H.row_node[r] + p->node_off[c]);
+            }
+            t0 += nt;
+        }
+        if ((st = upload(p, &D.Nt, tiled.data(), tiled.size()))) return st;
+        if ((st = upload(p, &D.tile_off, toff.data(), toff.size()))) return st;
+        if ((st = upload(p, &D.tile_k, tk.data(), tk.size()))) return st;
+        if ((st = upload(p, &D.row_node, rn.data(), rn.size()))) return st;
+    }
+    {   // Moebius rows: all components in one order, by level, then component, then row
+        const bool anti = (p->schedule == MZ_SCHED_ANTICHAIN);
+        int32_t maxlvl = 0;
+        for (const HostSide &H : Hs) maxlvl = std::max(maxlvl, anti ? H.nlevels : H.nulevels);
+        std::vector<int64_t> cnt((size_t)maxlvl + 2, 0);
+        for (const HostSide &H : Hs)
+            for (int64_t r = 0; r < H.n; ++r) cnt[(anti ? H.level : H.ulevel)[H.row_node[r]] + 1]++;
+        for (size_t l = 1; l < cnt.size(); ++l) cnt[l] += cnt[l - 1];
+        std::vector<std::pair<int32_t, int32_t>> order((size_t)D.n);   // (component, row)
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
+            const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
+            for (int64_t r = 0; r < H.n; ++r) order[(size_t)cnt[lvl[H.row_node[r]]]++] = {(int32_t)c, (int32_t)r};
+        }
+        std::vector<int64_t> moff((size_t)D.n);
+        std::vector<int32_t> mkp((size_t)D.n), mnode((size_t)D.n), mslot((size_t)D.n), mlevel((size_t)D.n);
+        size_t total = 0;
+        for (size_t i = 0; i < order.size(); ++i) {
+            const HostSide &H = Hs[order[i].first];
+            moff[i] = (int64_t)total;
+            mkp[i] = (H.k + 15) / 16 * 16;
+            total += (size_t)mkp[i];
+        }
+        std::vector<int32_t> Nm;
+        try {
+            Nm.assign(total, 0);      // padding in front of each row reads slot 0, a zero slot
+        } catch (...) {
+            set_last_error("host allocation failed");
+            return MZ_ERR_OOM;
+        }
+        // Each row lists its slots ordered by the level of the element in them (zero
+        // slots first): the kernel adds the latest-finishing ones last.
+        std::vector<std::pair<int32_t, int32_t>> cols;
+        for (size_t i = 0; i < order.size(); ++i) {
+            const size_t c = (size_t)order[i].first;
+            const int64_t r = order[i].second;
+            const HostSide &H = Hs[c];
+            const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
+            const int64_t k = H.k;
             const int32_t x = H.row_node[r];
             const int32_t cx = H.chain_id[x];
             const int32_t *src = &H.N[(size_t)r * k];
-            for (int64_t c = 0; c < k; ++c) {
-                const int32_t slot = (c == cx) ? (int32_t)H.chain_base[cx] : src[c];   // own chain: handled apart
+            cols.resize((size_t)k);
+            for (int64_t q = 0; q < k; ++q) {
+                const int32_t slot = (q == cx) ? (int32_t)H.chain_base[cx] : src[q];   // own chain: handled apart
                 const int32_t y = H.slot_node[slot];
-                cols[c] = {y < 0 ? -1 : lvl[y], slot};
+                cols[q] = {y < 0 ? -1 : lvl[y], slot + (int32_t)p->slot_off[c]};
             }
             std::stable_sort(cols.begin(), cols.end(),
                              [](const std::pair<int32_t, int32_t> &a, const std::pair<int32_t, int32_t> &b) {
                                  return a.first < b.first;
                              });
-            for (int64_t c = 0; c < k; ++c) Nm[(size_t)i * kp + (kp - k) + c] = cols[c].second;
-            mnode[i] = x;
-            mslot[i] = H.node_slot[x];
+            int32_t *dst = &Nm[(size_t)moff[i] + (mkp[i] - k)];
+            for (int64_t q = 0; q < k; ++q) dst[q] = cols[q].second;
+            mnode[i] = (int32_t)(x + p->node_off[c]);
+            mslot[i] = (int32_t)(H.node_slot[x] + p->slot_off[c]);
             mlevel[i] = lvl[x];
         }
         if ((st = upload(p, &D.Nm, Nm.data(), Nm.size()))) return st;
+        if ((st = upload(p, &D.mob_off, moff.data(), moff.size()))) return st;
+        if ((st = upload(p, &D.mob_kp, mkp.data(), mkp.size()))) return st;
         if ((st = upload(p, &D.mob_node, mnode.data(), mnode.size()))) return st;
         if ((st = upload(p, &D.mob_slot, mslot.data(), mslot.size()))) return st;
         if ((st = upload(p, &D.mob_level, mlevel.data(), mlevel.size()))) return st;
@@ -158,9 +212,9 @@ struct WsLayout {
     size_t counters = 0, flags = 0, agg = 0, inc = 0, P = 0, memset_bytes = 0, total = 0;
 };
 
-static WsLayout ws_layout(const HostSide &H, int32_t B) {
+static WsLayout ws_layout(const mz_plan *p, int32_t B) {
     WsLayout L;
-    const int64_t nslots = H.n + H.k;
+    const int64_t nslots = p->slots_total();
     L.sh = scan_shape(nslots, B);
     const size_t tiles = (size_t)L.sh.groups * (size_t)L.sh.ntiles;
     L.counters = 0;
@@ -200,13 +254,12 @@ static mz_status check_call(const mz_plan *p, int dtype, const void *in, const v
         set_last_error("batch must be >= 1");
         return MZ_ERR_INVALID_ARG;
     }
-    const HostSide &H = p->host[side];
-    *L = ws_layout(H, B);
+    *L = ws_layout(p, B);
     if (ws_bytes < L->total || ((uintptr_t)ws & 255)) {
         set_last_error("workspace too small or not 256-byte aligned");
         return MZ_ERR_INVALID_ARG;
     }
-    const size_t vb = (size_t)H.n * (size_t)B * 8;   // every dtype: 8 bytes per element
+    const size_t vb = (size_t)p->n_total() * (size_t)B * 8;   // every dtype: 8 bytes per element
     if (overlaps(in, vb, out, vb) || overlaps(in, vb, ws, ws_bytes) || overlaps(out, vb, ws, ws_bytes)) {
         set_last_error("input, output and workspace must not overlap");
         return MZ_ERR_INVALID_ARG;
@@ -226,7 +279,6 @@ static mz_status run_zeta(const mz_plan *p, int side, mz_dtype dtype, const void
     WsLayout L;
     mz_status st = check_call(p, dtype, f, g, B, ws, ws_bytes, side, &L);
     if (st) return st;
-    const HostSide &H = p->host[side];
     const DeviceSide &D = p->dev[side];
     cudaStream_t s = (cudaStream_t)stream;
     char *w = (char *)ws;
@@ -235,13 +287,13 @@ static mz_status run_zeta(const mz_plan *p, int side, mz_dtype dtype, const void
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     ScanArgs sa;
     sa.slot_node = D.slot_node;
-    sa.nslots = H.n + H.k;
+    sa.nslots = D.nslots;
     sa.B = B;
     sa.BW = L.sh.BW;
     sa.R = L.sh.R;
     sa.ntiles = L.sh.ntiles;
     sa.f = f;
-    sa.nB = H.n * (int64_t)B;
+    sa.nB = D.n * (int64_t)B;
     sa.P = w + L.P;
     sa.counters = (uint32_t *)(w + L.counters);
     sa.flags = (uint32_t *)(w + L.flags);
@@ -254,13 +306,14 @@ static mz_status run_zeta(const mz_plan *p, int side, mz_dtype dtype, const void
     mark_event(++g_last_launches, s);
     GatherArgs ga;
     ga.Nt = D.Nt;
+    ga.tile_off = D.tile_off;
+    ga.tile_k = D.tile_k;
     ga.row_node = D.row_node;
     ga.ntiles = D.ntiles;
-    ga.k = H.k;
     ga.B = B;
     ga.P = w + L.P;
     ga.g = g;
-    ga.nB = H.n * (int64_t)B;
+    ga.nB = D.n * (int64_t)B;
     if ((e = launch_gather(dtype, ga, p->num_sms, s)) != cudaSuccess) return cuda_fail(e, "niv gather launch");
     mark_event(++g_last_launches, s);
     return MZ_OK;
@@ -272,46 +325,112 @@ static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const vo
     WsLayout L;
     mz_status st = check_call(p, dtype, g, f, B, ws, ws_bytes, side, &L);
     if (st) return st;
-    const HostSide &H = p->host[side];
     const DeviceSide &D = p->dev[side];
     MobArgs ma;
     ma.Nm = D.Nm;
-    ma.kpad = D.kpad;
+    ma.mob_off = D.mob_off;
+    ma.mob_kp = D.mob_kp;
+    ma.kpad_max = D.kpad_max;
     ma.blocks_per_sm = p->mob_blocks_per_sm;
     ma.mob_node = D.mob_node;
     ma.mob_slot = D.mob_slot;
     ma.mob_level = D.mob_level;
     ma.pace_ns = p->mob_pace_ns;
-    ma.n = H.n;
-    ma.k = D.kpad;   // the Moebius kernels walk whole padded rows
+    ma.n = D.n;
     ma.B = B;
     ma.g = g;
     ma.f = f;
-    ma.nB = H.n * (int64_t)B;
+    ma.nB = D.n * (int64_t)B;
     ma.P = (unsigned long long *)((char *)ws + L.P);
     ma.status = p->d_status;
     ma.spin_limit = p->spin_limit;
     ma.withhold = p->withhold;
     int launches = 0;
     mark_event(0, (cudaStream_t)stream);
-    cudaError_t e = launch_mobius(dtype, ma, D.slot_node, H.n + H.k, p->schedule == MZ_SCHED_ANTICHAIN, p->num_sms,
+    cudaError_t e = launch_mobius(dtype, ma, D.slot_node, D.nslots, p->schedule == MZ_SCHED_ANTICHAIN, p->num_sms,
                                   (cudaStream_t)stream, &launches);
     g_last_launches = launches;
     if (e != cudaSuccess) return cuda_fail(e, "moebius launch");
     return MZ_OK;
 }
 
-}  // namespace mz
+// Builds the host side of every component (in parallel for many components) and
+// the offsets of the union.
+static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, const int64_t *m,
+                                  const int32_t *const *src, const int32_t *const *dst,
+                                  const int32_t *const *chain_id, bool dual) {
+    p->host[0].resize(count);
+    if (dual) p->host[1].resize(count);
+    std::vector<mz_status> sts(count, MZ_OK);
+    std::vector<std::string> errs(count);
+    auto work = [&](int32_t c) {
+        try {
+            std::vector<int32_t> s(src[c], src[c] + m[c]), d(dst[c], dst[c] + m[c]);
+            const int32_t *cid = chain_id ? chain_id[c] : nullptr;
+            sts[c] = build_host_side(n[c], s, d, cid, p->host[0][c], errs[c]);
+            if (sts[c] == MZ_OK && dual) {
+                // the dual poset: every edge flipped, the same chains (a chain of P is a chain of its dual)
+                sts[c] = build_host_side(n[c], d, s, p->host[0][c].chain_id.data(), p->host[1][c], errs[c]);
+                if (sts[c]) errs[c] = "dual: " + errs[c];
+            }
+        } catch (const std::bad_alloc &) {
+            sts[c] = MZ_ERR_OOM;
+            errs[c] = "host allocation failed";
+        }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int32_t nthreads = (int32_t)std::min<int64_t>(count, hw);
+    if (nthreads <= 1) {
+        for (int32_t c = 0; c < count; ++c) work(c);
+    } else {
+        std::atomic<int32_t> next{0};
+        std::vector<std::thread> pool;
+        for (int32_t t = 0; t < nthreads; ++t)
+            pool.emplace_back([&]() {
+                for (int32_t c = next++; c < count; c = next++) work(c);
+            });
+        for (auto &th : pool) th.join();
+    }
+    for (int32_t c = 0; c < count; ++c)
+        if (sts[c]) {
+            set_last_error(count > 1 ? "poset " + std::to_string(c) + ": " + errs[c] : errs[c]);
+            return sts[c];
+        }
+    p->node_off.assign(count + 1, 0);
+    p->slot_off.assign(count + 1, 0);
+    p->chain_off.assign(count + 1, 0);
+    for (int32_t c = 0; c < count; ++c) {
+        const HostSide &H = p->host[0][c];
+        p->node_off[c + 1] = p->node_off[c] + H.n;
+        p->chain_off[c + 1] = p->chain_off[c] + H.k;
+        p->slot_off[c + 1] = p->slot_off[c] + H.n + H.k;
+    }
+    if (p->slot_off[count] >= (int64_t)INT32_MAX) {
+        set_last_error("too many nodes plus chains for 32-bit slot indices");
+        return MZ_ERR_INVALID_ARG;
+    }
+    p->has_dual = dual;
+    return MZ_OK;
+}
 
-using namespace mz;
-
-extern "C" {
-
-mz_status mz_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *chain_id,
-                   const mz_build_opts *opts, mz_plan **out) {
+static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, const int32_t *const *src,
+                            const int32_t *const *dst, const int32_t *const *chain_id, const mz_build_opts *opts,
+                            mz_plan **out) {
     if (out) *out = nullptr;
-    if (!out || n < 1 || n > (int64_t(1) << 30) || m < 0 || (m > 0 && (!src || !dst))) {
+    if (!out || count < 1 || !n || !m || !src || !dst) {
         set_last_error("invalid sizes or null pointers");
+        return MZ_ERR_INVALID_ARG;
+    }
+    int64_t total = 0;
+    for (int32_t c = 0; c < count; ++c) {
+        if (n[c] < 1 || n[c] > (int64_t(1) << 30) || m[c] < 0 || (m[c] > 0 && (!src[c] || !dst[c]))) {
+            set_last_error("invalid sizes or null pointers" + (count > 1 ? " for poset " + std::to_string(c) : ""));
+            return MZ_ERR_INVALID_ARG;
+        }
+        total += n[c];
+    }
+    if (total > (int64_t(1) << 30)) {
+        set_last_error("more than 2^30 nodes in one plan");
         return MZ_ERR_INVALID_ARG;
     }
     mz_build_opts o;
@@ -328,26 +447,12 @@ mz_status mz_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     std::unique_ptr<mz_plan> p;
     try {
         p.reset(new mz_plan());
-        std::vector<int32_t> s(src, src + m), d(dst, dst + m);
-        std::string err;
-        mz_status st = build_host_side(n, s, d, chain_id, p->host[0], err);
-        if (st) {
-            set_last_error(err);
-            return st;
-        }
-        if (o.build_transpose) {
-            // the dual poset: every edge flipped, the same chains (a chain of P is a chain of its dual)
-            st = build_host_side(n, d, s, p->host[0].chain_id.data(), p->host[1], err);
-            if (st) {
-                set_last_error("dual: " + err);
-                return st;
-            }
-            p->has_dual = true;
-        }
     } catch (const std::bad_alloc &) {
         set_last_error("host allocation failed");
         return MZ_ERR_OOM;
     }
+    mz_status st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0);
+    if (st) return st;
     p->schedule = o.mobius_schedule;
     p->host_only = o.host_only != 0;
     if (o.spin_limit > 0) p->spin_limit = o.spin_limit;
@@ -362,19 +467,44 @@ mz_status mz_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
         e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-        mz_status st = MZ_OK;
         p->d_status = (uint32_t *)plan_alloc(p.get(), 256);
-        if (!p->d_status) st = MZ_ERR_OOM;
-        else if ((e = cudaMemset(p->d_status, 0, 256)) != cudaSuccess) st = cuda_fail(e, "cudaMemset");
+        if (!p->d_status) {
+            set_last_error("device allocation failed");
+            st = MZ_ERR_OOM;
+        } else if ((e = cudaMemset(p->d_status, 0, 256)) != cudaSuccess) {
+            st = cuda_fail(e, "cudaMemset");
+        }
         for (int side = 0; side < (p->has_dual ? 2 : 1) && st == MZ_OK; ++side) st = upload_side(p.get(), side);
         if (st) {
-            if (st == MZ_ERR_OOM) set_last_error("device allocation failed");
             plan_free_all(p.get());
             return st;
         }
     }
     *out = p.release();
     return MZ_OK;
+}
+
+}  // namespace mz
+
+using namespace mz;
+
+extern "C" {
+
+mz_status mz_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *chain_id,
+                   const mz_build_opts *opts, mz_plan **out) {
+    if (m > 0 && (!src || !dst)) {
+        if (out) *out = nullptr;
+        set_last_error("invalid sizes or null pointers");
+        return MZ_ERR_INVALID_ARG;
+    }
+    const int32_t *const cids[1] = {chain_id};
+    return build_plan(1, &n, &m, &src, &dst, chain_id ? cids : nullptr, opts, out);
+}
+
+mz_status mz_build_batch(int32_t count, const int64_t *n, const int64_t *m, const int32_t *const *src,
+                         const int32_t *const *dst, const int32_t *const *chain_id, const mz_build_opts *opts,
+                         mz_plan **out) {
+    return build_plan(count, n, m, src, dst, chain_id, opts, out);
 }
 
 void mz_destroy(mz_plan *plan) {
@@ -388,9 +518,7 @@ mz_status mz_workspace_size(const mz_plan *plan, mz_dtype dtype, int32_t batch, 
         set_last_error("invalid argument");
         return MZ_ERR_INVALID_ARG;
     }
-    size_t b = ws_layout(plan->host[0], batch).total;
-    if (plan->has_dual) b = std::max(b, ws_layout(plan->host[1], batch).total);
-    *bytes = b;
+    *bytes = ws_layout(plan, batch).total;   // primal and dual share the slot count
     return MZ_OK;
 }
 
@@ -417,7 +545,7 @@ mz_status mz_zeta_noalloc(const mz_plan *plan, mz_dtype dtype, const void *f, vo
         set_last_error("plan was built host-only");
         return MZ_ERR_NO_DEVICE;
     }
-    const size_t need = ws_layout(plan->host[0], batch).total;
+    const size_t need = ws_layout(plan, batch).total;
     if (need > MZ_NOALLOC_SCRATCH_BYTES) {
         set_last_error("mz_zeta_noalloc: this plan and batch need " + std::to_string(need) +
                        " bytes of scratch; the fixed scratch array holds " +
@@ -487,20 +615,22 @@ mz_status mz_check(const mz_plan *plan, mz_stream stream) {
 mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info) {
     if (!plan || !info) return MZ_ERR_INVALID_ARG;
     std::memset(info, 0, sizeof(*info));
-    const HostSide &H = plan->host[0];
-    info->n = H.n;
-    info->k = H.k;
+    info->n = plan->n_total();
+    info->k = (int32_t)plan->chain_off.back();
     info->has_transpose = plan->has_dual;
-    info->nnz = H.nnz;
-    info->edges = H.edges;
-    info->levels = H.nlevels;
-    info->ulevels = H.nulevels;
     info->schedule = plan->schedule;
-    if (plan->has_dual) {
-        info->levels_T = plan->host[1].nlevels;
-        info->ulevels_T = plan->host[1].nulevels;
+    info->components = (int32_t)plan->components();
+    for (const HostSide &H : plan->host[0]) {
+        info->nnz += H.nnz;
+        info->edges += H.edges;
+        info->levels = std::max(info->levels, H.nlevels);
+        info->ulevels = std::max(info->ulevels, H.nulevels);
+        info->max_chain = std::max(info->max_chain, H.max_chain);
     }
-    info->max_chain = H.max_chain;
+    for (const HostSide &H : plan->host[1]) {
+        info->levels_T = std::max(info->levels_T, H.nlevels);
+        info->ulevels_T = std::max(info->ulevels_T, H.nulevels);
+    }
     info->device_bytes = plan->device_bytes;
     return MZ_OK;
 }
@@ -510,38 +640,50 @@ mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *
         set_last_error("invalid argument");
         return MZ_ERR_INVALID_ARG;
     }
-    const HostSide &H = plan->host[dual ? 1 : 0];
-    const int64_t n = H.n, k = H.k;
-    std::vector<int32_t> tmp;
-    const int32_t *src = nullptr;
-    size_t count = (size_t)n;
-    switch (what) {
-        case MZ_EXPORT_CHAIN_ID: src = H.chain_id.data(); break;
-        case MZ_EXPORT_CHAIN_POS: src = H.chain_pos.data(); break;
-        case MZ_EXPORT_LEVEL: src = H.level.data(); break;
-        case MZ_EXPORT_ULEVEL: src = H.ulevel.data(); break;
-        case MZ_EXPORT_TOPO: src = H.topo.data(); break;
-        case MZ_EXPORT_NIV: {
-            count = (size_t)n * (size_t)k;
-            if (bytes < count * sizeof(int32_t)) break;
-            int32_t *o = (int32_t *)out;
-            for (int64_t x = 0; x < n; ++x) {
-                const int64_t cx = H.chain_id[x];
-                const int32_t *row = &H.N[(size_t)(H.node_slot[x] - cx - 1) * k];
-                for (int64_t c = 0; c < k; ++c)
-                    o[x * k + c] = row[c] == (int32_t)H.chain_base[c] ? -1 : H.slot_node[row[c]];
-            }
-            return MZ_OK;
-        }
-        default:
-            set_last_error("unknown export");
-            return MZ_ERR_INVALID_ARG;
+    const std::vector<HostSide> &Hs = plan->host[dual ? 1 : 0];
+    const int64_t n = plan->n_total();
+    if (what < MZ_EXPORT_CHAIN_ID || what > MZ_EXPORT_TOPO) {
+        set_last_error("unknown export");
+        return MZ_ERR_INVALID_ARG;
     }
-    if (bytes < count * sizeof(int32_t)) {
+    if (what == MZ_EXPORT_NIV) {
+        if (Hs.size() != 1) {
+            set_last_error("the niv map is exported for single-poset plans only");
+            return MZ_ERR_UNSUPPORTED;
+        }
+        const HostSide &H = Hs[0];
+        const int64_t k = H.k;
+        if (bytes < (size_t)n * (size_t)k * sizeof(int32_t)) {
+            set_last_error("output buffer too small");
+            return MZ_ERR_INVALID_ARG;
+        }
+        int32_t *o = (int32_t *)out;
+        for (int64_t x = 0; x < n; ++x) {
+            const int64_t cx = H.chain_id[x];
+            const int32_t *row = &H.N[(size_t)(H.node_slot[x] - cx - 1) * k];
+            for (int64_t c = 0; c < k; ++c)
+                o[x * k + c] = row[c] == (int32_t)H.chain_base[c] ? -1 : H.slot_node[row[c]];
+        }
+        return MZ_OK;
+    }
+    if (bytes < (size_t)n * sizeof(int32_t)) {
         set_last_error("output buffer too small");
         return MZ_ERR_INVALID_ARG;
     }
-    if (src) std::memcpy(out, src, count * sizeof(int32_t));
+    int32_t *o = (int32_t *)out;
+    for (size_t c = 0; c < Hs.size(); ++c) {
+        const HostSide &H = Hs[c];
+        int32_t *dst = o + plan->node_off[c];
+        for (int64_t x = 0; x < H.n; ++x) {
+            switch (what) {
+                case MZ_EXPORT_CHAIN_ID: dst[x] = H.chain_id[x] + (int32_t)plan->chain_off[c]; break;
+                case MZ_EXPORT_CHAIN_POS: dst[x] = H.chain_pos[x]; break;
+                case MZ_EXPORT_LEVEL: dst[x] = H.level[x]; break;
+                case MZ_EXPORT_ULEVEL: dst[x] = H.ulevel[x]; break;
+                default: dst[x] = H.topo[x] + (int32_t)plan->node_off[c]; break;   // MZ_EXPORT_TOPO
+            }
+        }
+    }
     return MZ_OK;
 }
 

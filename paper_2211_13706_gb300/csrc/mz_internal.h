@@ -39,23 +39,35 @@ struct HostSide {
     std::vector<int32_t> ulevel;     // [n] 0 = no dependency on another chain
 };
 
-// Device copies of one side (primal or dual).
+// Device copies of one side (primal or dual) for all components of the plan. The
+// components' slot spaces are concatenated (component p's slot s is global slot
+// slot_off[p] + s) and so are their node ids (node_off[p] + x).
 struct DeviceSide {
-    int32_t *slot_node = nullptr;  // [n + k]
-    int32_t *Nt = nullptr;         // [ntiles][k][32] tiled map for the zeta gather
-    int32_t *row_node = nullptr;   // [ntiles * 32], -1 for padding rows
-    int32_t *Nm = nullptr;         // [n][k] rows in Moebius processing order; own column -> zero slot
-    int32_t *mob_node = nullptr;   // [n] node of the i-th processed row
-    int32_t *mob_slot = nullptr;   // [n] its slot
-    int32_t *mob_level = nullptr;  // [n] its level in the schedule
+    int64_t n = 0;                 // nodes of all components
+    int64_t nslots = 0;            // n + total number of chains
+    int32_t *slot_node = nullptr;  // [nslots] global node or -1 (zero slot), padded to 64 entries
+    int32_t *Nt = nullptr;         // tiles of 32 rows, column-major in a tile, concatenated
+    int64_t *tile_off = nullptr;   // [ntiles] start of each tile in Nt
+    int32_t *tile_k = nullptr;     // [ntiles] row length (k of the tile's component)
+    int32_t *row_node = nullptr;   // [ntiles * 32] global node of each tile row, -1 for padding
     int64_t ntiles = 0;
-    int32_t kpad = 0;              // Moebius row length (k rounded up to 16)
+    int32_t *Nm = nullptr;         // Moebius rows in processing order, concatenated
+    int64_t *mob_off = nullptr;    // [n] start of the i-th processed row in Nm
+    int32_t *mob_kp = nullptr;     // [n] its length: k of its component rounded up to 16
+    int32_t *mob_node = nullptr;   // [n] global node of the i-th processed row
+    int32_t *mob_slot = nullptr;   // [n] its global slot
+    int32_t *mob_level = nullptr;  // [n] its level in the schedule
+    int32_t kpad_max = 0;
+    int32_t k_max = 0;
 };
 
 }  // namespace mz
 
 struct mz_plan {
-    mz::HostSide host[2];
+    std::vector<mz::HostSide> host[2];   // per component: primal, dual
+    std::vector<int64_t> node_off;       // [components + 1]
+    std::vector<int64_t> slot_off;       // [components + 1] (same for both sides)
+    std::vector<int64_t> chain_off;      // [components + 1]
     mz::DeviceSide dev[2];
     bool has_dual = false;
     bool host_only = false;
@@ -72,6 +84,10 @@ struct mz_plan {
     void *(*dev_alloc)(size_t, void *) = nullptr;
     void (*dev_free)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
+
+    int64_t n_total() const { return node_off.back(); }
+    int64_t slots_total() const { return slot_off.back(); }
+    size_t components() const { return host[0].size(); }
 };
 
 namespace mz {

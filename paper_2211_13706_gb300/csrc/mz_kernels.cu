@@ -85,37 +85,6 @@ __device__ __forceinline__ unsigned long long wait_value(const unsigned long lon
     }
 }
 
-// Wait until none of the NV words v[j] (read from P[idx[j]], idx[j] >= 0) is the
-// sentinel. Every round re-issues all missing loads together, so a lane pays
-// about one round trip after its last value lands, whatever the number missing.
-template <int NV>
-__device__ __forceinline__ void wait_values(unsigned long long *v, const int32_t *idx, const unsigned long long *P,
-                                            unsigned long long sentinel, uint32_t *status, int64_t limit) {
-    for (int64_t it = 0;; ++it) {
-        bool missing = false;
-#pragma unroll
-        for (int j = 0; j < NV; ++j) missing |= (idx[j] >= 0 && v[j] == sentinel);
-        if (!missing) return;
-        if ((it & 255) == 255 && ld_relaxed_u32(status)) {
-#pragma unroll
-            for (int j = 0; j < NV; ++j)
-                if (v[j] == sentinel) v[j] = 0ull;
-            return;
-        }
-        if (it >= limit) {
-            report(status, MZ_ERR_TIMEOUT);
-#pragma unroll
-            for (int j = 0; j < NV; ++j)
-                if (v[j] == sentinel) v[j] = 0ull;
-            return;
-        }
-        if (it > 256) __nanosleep(32);
-#pragma unroll
-        for (int j = 0; j < NV; ++j)
-            if (idx[j] >= 0 && v[j] == sentinel) v[j] = ld_relaxed_u64(P + idx[j]);
-    }
-}
-
 // ---------------------------------------------------------------- chain scan (V f)
 constexpr int kScanThreads = 256;
 constexpr int kScanSeg = 16;  // slots per thread
@@ -274,9 +243,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t b0 = (int64_t)blockIdx.y * BT;
     const P_t *__restrict__ P = reinterpret_cast<const P_t *>(a.P);
-    const int k = a.k;
     for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
-        const int32_t *__restrict__ np = a.Nt + tile * (int64_t)k * kTileRows + lane;
+        const int k = a.tile_k[tile];
+        const int32_t *__restrict__ np = a.Nt + a.tile_off[tile] + lane;
         Acc acc[BT];
 #pragma unroll
         for (int u = 0; u < BT; ++u) acc[u] = Pol::acc_zero();
@@ -319,10 +288,10 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const P_t *__restrict__ P = reinterpret_cast<const P_t *>(a.P);
-    const int k = a.k;
     const int64_t B = a.B;
     for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
-        const int32_t *__restrict__ nt = a.Nt + tile * (int64_t)k * kTileRows;
+        const int k = a.tile_k[tile];
+        const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
         for (int r = sub; r < kTileRows; r += R) {
             const int32_t node = a.row_node[tile * kTileRows + r];
             if (node < 0) continue;
@@ -355,133 +324,6 @@ __global__ void k_mob_init(const int32_t *__restrict__ slot_node, int64_t nslots
 template <class T>
 __device__ __forceinline__ T shfl_xor_t(T v, int off) {
     return __shfl_xor_sync(0xffffffffu, v, off);
-}
-
-// One warp per row, B == 1. The host orders every row of the map by the level
-// of the dependency (earliest first), so the last kLate columns hold the
-// dependencies that finish last. Lanes sum the early columns (usually ready at
-// once) and reduce them into lane 0 while lane 0 waits for the late ones; after
-// the last dependency lands only a few additions stand between it and the
-// store. The next row of the warp (map entries, node, slot) is loaded while the
-// current one waits, and its g value right after the current store.
-constexpr int kLate = 8;
-
-template <class M, bool ANTI, int KMAX>
-__device__ __forceinline__ void wave_b1(const MobArgs &a, int64_t warp, int64_t nwarps, int lane) {
-    using T = typename M::T;
-    const int k = a.k;
-    const int kearly = k > kLate ? k - kLate : 0;
-    unsigned long long *P = a.P;
-    const unsigned long long SENT = M::kSentinel;
-    int32_t idx[KMAX], nidx[KMAX], late[kLate], nlate[kLate];
-    int64_t i = warp;
-    if (i >= a.n) return;
-    auto load_row = [&](int64_t r, int32_t *out, int32_t *lt) {
-        const int32_t *row = a.Nm + r * (int64_t)k;
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) {
-            const int c = lane + 32 * j;
-            out[j] = c < kearly ? __ldcs(row + c) : -1;
-        }
-#pragma unroll
-        for (int j = 0; j < kLate; ++j) lt[j] = (lane == 0 && kearly + j < k) ? __ldcs(row + kearly + j) : -1;
-    };
-    load_row(i, idx, late);
-    int64_t node = a.mob_node[i], sout = a.mob_slot[i];
-    T gx = lane == 0 ? M::load_in(a.g, node, a.nB) : T(0);
-    for (; i < a.n; i += nwarps) {
-        unsigned long long v[KMAX], lv[kLate];
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) v[j] = idx[j] >= 0 ? ld_relaxed_u64(P + idx[j]) : 0ull;
-#pragma unroll
-        for (int j = 0; j < kLate; ++j) lv[j] = late[j] >= 0 ? ld_relaxed_u64(P + late[j]) : 0ull;
-        unsigned long long vprev = 0;
-        if (ANTI && lane == 0) vprev = ld_relaxed_u64(P + sout - 1);
-        const int64_t inext = i + nwarps;
-        int64_t nnode = 0, nsout = 0;
-        if (inext < a.n) {
-            load_row(inext, nidx, nlate);
-            nnode = a.mob_node[inext];
-            nsout = a.mob_slot[inext];
-        }
-        // early columns: every lane, then a reduction into lane 0
-        wait_values<KMAX>(v, idx, P, SENT, a.status, a.spin_limit);
-        T acc = T(0);
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j)
-            if (idx[j] >= 0) acc = M::add(acc, M::from_bits(v[j]));
-        // late values still missing: ask again now, so the answers arrive during the reduction
-#pragma unroll
-        for (int j = 0; j < kLate; ++j)
-            if (late[j] >= 0 && lv[j] == SENT) lv[j] = ld_relaxed_u64(P + late[j]);
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) acc = M::add(acc, __shfl_down_sync(0xffffffffu, acc, off));
-        if (lane == 0) {
-            // late columns, latest last
-            wait_values<kLate>(lv, late, P, SENT, a.status, a.spin_limit);
-#pragma unroll
-            for (int j = 0; j < kLate; ++j)
-                if (late[j] >= 0) acc = M::add(acc, M::from_bits(lv[j]));
-            const bool publish = (i != a.withhold);
-            if (ANTI) {
-                if (vprev == SENT) vprev = wait_value(P + sout - 1, SENT, a.status, a.spin_limit);
-                const T prev = M::from_bits(vprev);
-                const T fx = M::sub(gx, M::add(acc, prev));
-                if (publish) st_relaxed_u64(P + sout, M::to_bits(M::add(prev, fx)));
-                M::store_out(a.f, node, a.nB, fx);
-            } else if (publish) {
-                st_relaxed_u64(P + sout, M::to_bits(M::sub(gx, acc)));
-            }
-            if (inext < a.n) gx = M::load_in(a.g, nnode, a.nB);
-        }
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) idx[j] = nidx[j];
-#pragma unroll
-        for (int j = 0; j < kLate; ++j) late[j] = nlate[j];
-        node = nnode;
-        sout = nsout;
-    }
-}
-
-// Waits, in column order, for each word that still holds the sentinel: polls the
-// first missing one, and once it lands asks again for every later missing one
-// in a single round. Columns are sorted by dependency level, so words tend to
-// land in order; a thread sends one request per round instead of one per word.
-template <int NV>
-__device__ __forceinline__ void wait_in_order(unsigned long long *v, const int32_t *id, const unsigned long long *P,
-                                              unsigned long long sentinel, uint32_t *status, int64_t limit) {
-    // bit j of `miss` set while v[j] holds the sentinel; all indexing stays static
-    uint32_t miss = 0;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) miss |= (v[j] == sentinel ? 1u : 0u) << j;
-    for (int64_t it = 0; miss; ++it) {
-        const int first = __ffs(miss) - 1;
-        bool landed = false;
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            if (j == first) {
-                v[j] = ld_relaxed_u64(P + id[j]);
-                landed = v[j] != sentinel;
-            }
-        }
-        if (landed) {   // ask again, in one round, for every later word still missing
-#pragma unroll
-            for (int j = 0; j < NV; ++j)
-                if (j > first && ((miss >> j) & 1u)) v[j] = ld_relaxed_u64(P + id[j]);
-        }
-        miss = 0;
-#pragma unroll
-        for (int j = 0; j < NV; ++j) miss |= (v[j] == sentinel ? 1u : 0u) << j;
-        if (!miss) return;
-        if (((it & 255) == 255 && ld_relaxed_u32(status)) || it >= limit) {
-            if (it >= limit) report(status, MZ_ERR_TIMEOUT);
-#pragma unroll
-            for (int j = 0; j < NV; ++j)
-                if (v[j] == sentinel) v[j] = 0ull;
-            return;
-        }
-        if (!landed && it > 128) __nanosleep(64);
-    }
 }
 
 // Sums the NV words v[j] = P[id[j]] into acc (or subtracts them, SUB) in column order, adding each one as
@@ -557,12 +399,12 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
     const int64_t grp = tid / G, ngrp = nthreads / G;
     const int b0 = (int)(tid % G);
     const int64_t B = (G == 1) ? 1 : a.B;
-    const int kp = a.kpad;
     unsigned long long *P = a.P;
     const unsigned long long SENT = M::kSentinel;
     int32_t done_level = 0;   // level of the row this group finished last (the frontier was there)
     for (int64_t i = grp; i < a.n; i += ngrp) {
-        const int32_t *row = a.Nm + i * (int64_t)kp;
+        const int32_t *row = a.Nm + a.mob_off[i];
+        const int kp = a.mob_kp[i];
         const int32_t level = a.mob_level[i];
         // The dependencies of this row sit at least one level lower; levels finish one
         // after the other, so sleep through the ones that must come first.
@@ -575,8 +417,9 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
             }
         }
         if (b0 == 0 && i + ngrp < a.n) {
-            const char *nxt = reinterpret_cast<const char *>(row + ngrp * (int64_t)kp);
-            for (int c = 0; c < kp * 4; c += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + c));
+            const char *nxt = reinterpret_cast<const char *>(a.Nm + a.mob_off[i + ngrp]);
+            const int nkp = a.mob_kp[i + ngrp];
+            for (int c = 0; c < nkp * 4; c += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + c));
         }
         const int64_t node = a.mob_node[i];
         const int64_t sout = a.mob_slot[i];
@@ -654,26 +497,18 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
     }
 }
 
-template <class M, bool ANTI, int KMAX>
-__global__ void __launch_bounds__(256) k_mob_wave_b1(MobArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    wave_b1<M, ANTI, KMAX>(a, warp, nwarps, lane);
-}
-
 template <class M, bool ANTI>
 __global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
     using T = typename M::T;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int k = a.k;
     const int32_t B = a.B;
     unsigned long long *P = a.P;
     const unsigned long long SENT = M::kSentinel;
     for (int64_t i = warp; i < a.n; i += nwarps) {
-        const int32_t *__restrict__ row = a.Nm + i * (int64_t)k;
+        const int32_t *__restrict__ row = a.Nm + a.mob_off[i];
+        const int k = a.mob_kp[i];
         const int64_t node = a.mob_node[i];
         const int64_t sout = a.mob_slot[i];
         const bool publish = (i != a.withhold);
@@ -819,7 +654,7 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     int threads = 256;
     // rows per thread group: G = 1 for one function, G = min(B, 32) for a power-of-two batch
     const bool pow2 = (a.B & (a.B - 1)) == 0;
-    const bool per_thread = pow2 && (int64_t)a.B * (a.n + a.k) < ((int64_t)1 << 31);
+    const bool per_thread = pow2 && (int64_t)a.B * nslots < ((int64_t)1 << 31);
     int G = 1;
     if (per_thread) {
         threads = 128;
@@ -834,8 +669,6 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
             default: fn = MZ_WAVE_G(32); break;
         }
 #undef MZ_WAVE_G
-    } else if (a.B == 1 && a.k <= 256 + kLate) {
-        fn = anti ? (void *)k_mob_wave_b1<M, true, 8> : (void *)k_mob_wave_b1<M, false, 8>;
     } else {
         fn = anti ? (void *)k_mob_wave<M, true> : (void *)k_mob_wave<M, false>;
     }

@@ -35,24 +35,28 @@ struct ScanArgs {
 
 struct GatherArgs {
     const int32_t *Nt;
+    const int64_t *tile_off;  // [ntiles] start of each tile in Nt
+    const int32_t *tile_k;    // [ntiles] row length of each tile
     const int32_t *row_node;
     int64_t ntiles;
-    int32_t k, B;
+    int32_t B;
     const void *P;
     void *g;
     int64_t nB;
 };
 
 struct MobArgs {
-    const int32_t *Nm;       // [n][kpad] rows in processing order
-    int32_t kpad;            // row length: k rounded up to a multiple of 16
-    int32_t blocks_per_sm;   // one-thread-per-row kernel: resident blocks of 128 per SM
+    const int32_t *Nm;          // rows in processing order, concatenated
+    const int64_t *mob_off;     // [n] start of each row in Nm
+    const int32_t *mob_kp;      // [n] its length (a multiple of 16)
+    int32_t kpad_max;           // longest row
+    int32_t blocks_per_sm;      // one-thread-per-row kernel: resident blocks of 128 per SM
     const int32_t *mob_node;
     const int32_t *mob_slot;
     const int32_t *mob_level;   // level of each processed row
     int32_t pace_ns;            // sleep per level of distance before polling (0: none)
     int64_t n;
-    int32_t k, B;
+    int32_t B;
     const void *g;
     void *f;
     int64_t nB;
