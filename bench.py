@@ -51,6 +51,14 @@ WORKLOADS = {
     "c3": dict(n=1 << 22, k=128, cross_deg=2,
                desc="planted poset n=2^22, k=128 chains of 32768, cross-chain out-degree 2"),
 }
+BATCH_WORKLOADS = {
+    "c4": dict(count=4096, batch=32, cross_deg=2,
+               desc="4096 planted posets, n log-uniform [1k,64k], k log-uniform [4,256], cross out-degree 2, "
+                    "B=32 functions per poset"),
+    "c4s": dict(count=256, batch=32, cross_deg=2,
+                desc="256 planted posets drawn like the 4096-poset batch (n log-uniform [1k,64k], "
+                     "k log-uniform [4,256], cross out-degree 2), B=32 functions per poset"),
+}
 DTYPES = {"f64": ("f64u", "fp64 uniform [-1,1]"), "i64": ("i64:1048576", "int64 uniform [-2^20,2^20]"),
           "f32c": ("f32u", "fp32 uniform [-1,1] as F32C pairs")}
 
@@ -270,6 +278,99 @@ def cpu_baseline(p, f_np, budget_s: float, max_rows: int):
                       "the oracle's Moebius has no per-row form cheaper than O(|out(x)|^2)"}
 
 
+def _gen_one(spec_and_deg):
+    (n, k, seed), deg = spec_and_deg
+    p = pg.planted_chain_poset(n, k, seed, cross_deg=deg)
+    return p.n, p.src, p.dst, p.chain_id
+
+
+def gen_batch_posets(wl: str, seed: int):
+    """The posets of a batch workload, generated in a spawned process pool (started
+    before this process touches the GPU)."""
+    import multiprocessing as mp
+    w = BATCH_WORKLOADS[wl]
+    specs = pg.planted_batch_specs(w["count"], seed)
+    work = [(sp, w["cross_deg"]) for sp in specs]
+    if w["count"] <= 64:
+        return [_gen_one(x) for x in work]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen_one, work, chunksize=16)
+
+
+def time_batch(mz, plan, x, steps, warmup, torch, use_graph):
+    """zeta then Moebius of x per step, replayed from a captured CUDA graph when
+    use_graph (else launched directly); returns (total device ms of `steps` steps, graph used)."""
+    g = torch.empty_like(x)
+    y = torch.empty_like(x)
+    step = lambda: (plan.zeta(x, out=g), plan.mobius(g, out=y))
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    graph = None
+    if use_graph:
+        try:
+            cg = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                step()                       # warm the workspace on the capture stream
+            torch.cuda.current_stream().wait_stream(side)
+            with torch.cuda.graph(cg):
+                step()
+            graph = cg
+        except Exception as exc:            # capture unsupported: launch directly
+            print(f"graph capture failed ({exc}); timing direct launches", file=sys.stderr)
+            torch.cuda.synchronize()
+            graph = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for _ in range(steps):
+        e0.record()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+        e1.record()
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    plan.check()
+    return total, graph is not None
+
+
+def batch_values(n, B, dtype_key, seed, torch):
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    if dtype_key == "f32c":
+        hi = torch.rand((n, B), generator=gen, device="cuda", dtype=torch.float32) * 2 - 1
+        return torch.stack([hi, torch.zeros_like(hi)])
+    if dtype_key == "f64":
+        return torch.rand((n, B), generator=gen, device="cuda", dtype=torch.float64) * 2 - 1
+    return torch.randint(-1000, 1001, (n, B), generator=gen, device="cuda", dtype=torch.int64)
+
+
+def run_batch_workload(mz, wl, posets, steps, warmup, torch, dtypes=("f32c", "f64"), graph=True):
+    """Builds one plan for all posets, autotunes it and times each dtype."""
+    from paper_2211_13706_gb300 import autotune
+    w = BATCH_WORKLOADS[wl]
+    t0 = time.perf_counter()
+    plan = mz.Plan.batch([(n, s_, d_, c) for n, s_, d_, c in posets])
+    build_s = time.perf_counter() - t0
+    info = plan.info
+    out = {"workload": w["desc"], "posets": info["components"], "n_total": info["n"], "k_total": info["k"],
+           "nnz": info["nnz"], "max_ulevels": info["ulevels"], "batch": w["batch"], "host_build_s": round(build_s, 1)}
+    for dk in dtypes:
+        x = batch_values(info["n"], w["batch"], dk, 11, torch)
+        tuned = autotune.tune(plan, x)
+        tot, used_graph = time_batch(mz, plan, x, steps, warmup, torch, graph)
+        units = 2 * info["n"] * w["batch"] * steps
+        out[dk] = {"value": round(units / (tot / 1e3), 1), "unit": UNIT, "ms_per_step": round(tot / steps, 3),
+                   "steps": steps, "cuda_graph": used_graph, "tuning": tuned}
+        del x
+        torch.cuda.empty_cache()
+    plan.close()
+    return out
+
+
 def device_arm(args):
     import torch
     import paper_2211_13706_gb300 as mz
@@ -277,6 +378,12 @@ def device_arm(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # batch-workload posets: generated before this process touches the GPU
+    batch_posets = None
+    if args.workload in BATCH_WORKLOADS:
+        return batch_arm(args, gen_batch_posets(args.workload, 1 + rank))
+    if not args.no_variants:
+        batch_posets = gen_batch_posets("c4s", 1 + rank)
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -361,6 +468,9 @@ def device_arm(args):
                             "kernels_ms": {a: round(b, 5) for a, b in ktv.items()}}
         pa = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
         kta, tot, _, _, _, _ = time_transforms(mz, pa, x, 3, 1, torch, flush, anti=True)
+        if batch_posets is not None:
+            variants["batched_c4s"] = run_batch_workload(mz, "c4s", batch_posets, args.variant_steps // 5 or 3,
+                                                         3, torch)
         variants["mobius_antichain_schedule_" + args.dtype] = {
             "mobius_ms": round(kta["mob_init"] + kta["mob_wave"], 4), "levels": pa.info["levels"],
             "note": "Alg. 5/6 schedule (antichain levels) instead of U's dependency levels"}
@@ -395,13 +505,61 @@ def device_arm(args):
         dist.destroy_process_group()
 
 
+def batch_arm(args, posets):
+    """--workload c4 / c4s: many posets in one plan, B functions each; one JSON line."""
+    import torch
+    import paper_2211_13706_gb300 as mz
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0"))))
+    dk = args.dtype if args.dtype != "f64" or args.batch_dtype_f64 else "f32c"
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    res = run_batch_workload(mz, args.workload, posets, args.steps, args.warmup, torch,
+                             dtypes=(dk, "f64") if dk != "f64" else ("f64",))
+    clocks = sampler.stop()
+    main = res[dk]
+    tot_ms = main["ms_per_step"] * main["steps"]
+    if dist:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    value = 2 * res["n_total"] * res["batch"] * main["steps"] * world / (tot_ms / 1e3)
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": main["steps"],
+            "warmup": args.warmup, "ms_per_step": round(tot_ms / main["steps"], 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dk, "data": "synthetic",
+            "config": {"workload": res["workload"], "posets": res["posets"], "n_total": res["n_total"],
+                       "k_total": res["k_total"], "batch": res["batch"], "nnz": res["nnz"],
+                       "max_ulevels": res["max_ulevels"], "l2": "inputs larger than L2",
+                       "units": "2*n*B node-values per step", "host_build_s": res["host_build_s"],
+                       "cuda_graph": main["cuda_graph"], "tuning": main["tuning"],
+                       "parallelism": f"replicas x{world}"},
+            "fp64_plain": res.get("f64"), "clocks": clocks, "gpu_launches": 5 * main["steps"]}
+    print(json.dumps(line))
+
+
 # ----------------------------------------------------------------------------- reference arm
 def reference_arm(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     import oracle
-    wl = WORKLOADS[args.workload]
-    p = make_poset(args.workload, 1)
+    if args.workload in BATCH_WORKLOADS:
+        # a batch workload: each step is one exact zeta row of one of its posets
+        bw = BATCH_WORKLOADS[args.workload]
+        specs = pg.planted_batch_specs(bw["count"], 1)
+        n_, k_, sd = specs[0]
+        p = pg.planted_chain_poset(n_, k_, sd, cross_deg=bw["cross_deg"])
+        wl = {"desc": bw["desc"] + f" (rows of its first poset, n={n_}, k={k_})", "k": k_}
+    else:
+        wl = WORKLOADS[args.workload]
+        p = make_poset(args.workload, 1)
     kind, fdesc = DTYPES[args.dtype]
     f_np = pg.function_values(p.n, 1, kind, 2)[:, 0]
     if args.dtype == "f32c":
@@ -434,7 +592,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["mz", "reference"], default="mz")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS), default="c2")
+    ap.add_argument("--batch-dtype-f64", action="store_true", help="batch workloads: time fp64 as the main line")
     ap.add_argument("--dtype", choices=sorted(DTYPES), default="f64")
     ap.add_argument("--variant-steps", type=int, default=50)
     ap.add_argument("--no-variants", action="store_true")

@@ -248,6 +248,18 @@ mz_status mz_mobius_T(const mz_plan *plan, mz_dtype dtype, const void *h, void *
  */
 mz_status mz_check(const mz_plan *plan, mz_stream stream);
 
+/* Launch shapes a plan uses; mz_plan_tune changes them after the build (0 keeps a
+   value). An autotuner times transforms under candidate shapes and keeps the best. */
+typedef struct {
+    int32_t mobius_blocks_per_sm; /* as mz_build_opts::mobius_blocks_per_sm (default 2) */
+    int32_t mobius_pace_ns;       /* as mz_build_opts::mobius_pace_ns (default 1000; < 0 = none) */
+    int32_t gather_blocks_per_sm; /* resident 256-thread blocks per SM of the zeta gather (default 32) */
+    int32_t reserved;
+} mz_tuning;
+
+/* Sets the plan's launch shapes (results are unaffected); fills *current if non-NULL. */
+mz_status mz_plan_tune(mz_plan *plan, const mz_tuning *set, mz_tuning *current);
+
 /* Fills *info (host data only). */
 mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info);
 

@@ -35,7 +35,7 @@ MZ_EXPORT_CHAIN_ID, MZ_EXPORT_CHAIN_POS, MZ_EXPORT_NIV, MZ_EXPORT_LEVEL, MZ_EXPO
 # every symbol include/mz.h declares
 EXPORTED = ["mz_build", "mz_build_batch", "mz_destroy", "mz_workspace_size", "mz_zeta", "mz_zeta_noalloc", "mz_mobius",
             "mz_zeta_T", "mz_mobius_T",
-            "mz_check", "mz_plan_info", "mz_plan_export", "mz_last_launch_count", "mz_set_launch_events",
+            "mz_check", "mz_plan_tune", "mz_plan_info", "mz_plan_export", "mz_last_launch_count", "mz_set_launch_events",
             "mz_status_string", "mz_last_error"]
 
 
@@ -51,6 +51,14 @@ class _Opts(ctypes.Structure):
                 ("mobius_pace_ns", ctypes.c_int32), ("reserved1", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("debug_withhold", ctypes.c_int64),
                 ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("mobius_blocks_per_sm", ctypes.c_int32), ("mobius_pace_ns", ctypes.c_int32),
+                ("gather_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
 class PlanInfo(ctypes.Structure):
@@ -78,6 +86,7 @@ def _load():
     lib.mz_zeta_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, i32, vp]
     lib.mz_check.argtypes = [vp, vp]
     lib.mz_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    lib.mz_plan_tune.argtypes = [vp, ctypes.POINTER(Tuning), ctypes.POINTER(Tuning)]
     lib.mz_plan_export.argtypes = [vp, i32, i32, vp, sz]
     lib.mz_last_launch_count.argtypes = []
     lib.mz_last_launch_count.restype = i32
@@ -189,6 +198,15 @@ def mz_mobius_T(plan, dtype, h_ptr, r_ptr, batch, ws_ptr, ws_bytes, stream=0):
 
 def mz_check(plan: int, stream: int = 0) -> None:
     _check(lib.mz_check(plan, stream), "mz_check")
+
+
+def mz_plan_tune(plan: int, mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0,
+                 gather_blocks_per_sm: int = 0) -> dict:
+    """mz_plan_tune: sets the given launch shapes (0 keeps one) and returns the current ones."""
+    cur = Tuning()
+    want = Tuning(int(mobius_blocks_per_sm), int(mobius_pace_ns), int(gather_blocks_per_sm), 0)
+    _check(lib.mz_plan_tune(plan, ctypes.byref(want), ctypes.byref(cur)), "mz_plan_tune")
+    return cur.as_dict()
 
 
 def mz_plan_info(plan: int) -> dict:

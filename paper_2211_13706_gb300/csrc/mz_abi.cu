@@ -75,6 +75,21 @@ static mz_status upload(mz_plan *p, T **dst, const T *src, size_t count) {
     return MZ_OK;
 }
 
+// Runs fn(begin, end) over [0, count) split into contiguous pieces on the host's threads.
+template <class F>
+static void parallel_for(int64_t count, F fn) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t pieces = std::min<int64_t>(hw, std::max<int64_t>(1, count / 4096));
+    if (pieces <= 1) {
+        fn((int64_t)0, count);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int64_t t = 0; t < pieces; ++t)
+        pool.emplace_back([&, t]() { fn(count * t / pieces, count * (t + 1) / pieces); });
+    for (auto &th : pool) th.join();
+}
+
 // Device layouts of one side (all components): the concatenated slot map, the
 // tiled niv map for the zeta gather, and the map in Moebius processing order.
 static mz_status upload_side(mz_plan *p, int side) {
@@ -119,20 +134,26 @@ static mz_status upload_side(mz_plan *p, int side) {
             set_last_error("host allocation failed");
             return MZ_ERR_OOM;
         }
-        int64_t t0 = 0;
-        for (size_t c = 0; c < C; ++c) {
-            const HostSide &H = Hs[c];
-            const int64_t k = H.k, nt = (H.n + kTileRows - 1) / kTileRows;
-            const int32_t so = (int32_t)p->slot_off[c];
-            for (int64_t r = 0; r < H.n; ++r) {
-                const int64_t t = t0 + r / kTileRows, lane = r % kTileRows;
-                int32_t *dst = &tiled[(size_t)toff[t] + lane];
-                const int32_t *row = &H.N[(size_t)r * k];
-                for (int64_t q = 0; q < k; ++q) dst[q * kTileRows] = row[q] + so;
-                rn[(size_t)t * kTileRows + lane] = (int32_t)(H.row_node[r] + p->node_off[c]);
+        std::vector<int64_t> tile0(C + 1, 0);   // first tile of each component
+        for (size_t c = 0; c < C; ++c) tile0[c + 1] = tile0[c] + (Hs[c].n + kTileRows - 1) / kTileRows;
+        parallel_for((int64_t)C == 1 ? Hs[0].n : (int64_t)C, [&](int64_t lo, int64_t hi) {
+            // one poset: split its rows; many posets: split the posets
+            const bool rows = (C == 1);
+            for (int64_t u = lo; u < hi; ++u) {
+                const size_t c = rows ? 0 : (size_t)u;
+                const HostSide &H = Hs[c];
+                const int64_t k = H.k;
+                const int32_t so = (int32_t)p->slot_off[c];
+                const int64_t r0 = rows ? u : 0, r1 = rows ? u + 1 : H.n;
+                for (int64_t r = r0; r < r1; ++r) {
+                    const int64_t t = tile0[c] + r / kTileRows, lane = r % kTileRows;
+                    int32_t *dst = &tiled[(size_t)toff[t] + lane];
+                    const int32_t *row = &H.N[(size_t)r * k];
+                    for (int64_t q = 0; q < k; ++q) dst[q * kTileRows] = row[q] + so;
+                    rn[(size_t)t * kTileRows + lane] = (int32_t)(H.row_node[r] + p->node_off[c]);
+                }
             }
-            t0 += nt;
-        }
+        });
         if ((st = upload(p, &D.Nt, tiled.data(), tiled.size()))) return st;
         if ((st = upload(p, &D.tile_off, toff.data(), toff.size()))) return st;
         if ((st = upload(p, &D.tile_k, tk.data(), tk.size()))) return st;
@@ -170,32 +191,34 @@ static mz_status upload_side(mz_plan *p, int side) {
         }
         // Each row lists its slots ordered by the level of the element in them (zero
         // slots first): the kernel adds the latest-finishing ones last.
-        std::vector<std::pair<int32_t, int32_t>> cols;
-        for (size_t i = 0; i < order.size(); ++i) {
-            const size_t c = (size_t)order[i].first;
-            const int64_t r = order[i].second;
-            const HostSide &H = Hs[c];
-            const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
-            const int64_t k = H.k;
-            const int32_t x = H.row_node[r];
-            const int32_t cx = H.chain_id[x];
-            const int32_t *src = &H.N[(size_t)r * k];
-            cols.resize((size_t)k);
-            for (int64_t q = 0; q < k; ++q) {
-                const int32_t slot = (q == cx) ? (int32_t)H.chain_base[cx] : src[q];   // own chain: handled apart
-                const int32_t y = H.slot_node[slot];
-                cols[q] = {y < 0 ? -1 : lvl[y], slot + (int32_t)p->slot_off[c]};
+        parallel_for((int64_t)order.size(), [&](int64_t lo, int64_t hi) {
+            std::vector<std::pair<int32_t, int32_t>> cols;
+            for (int64_t i = lo; i < hi; ++i) {
+                const size_t c = (size_t)order[i].first;
+                const int64_t r = order[i].second;
+                const HostSide &H = Hs[c];
+                const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
+                const int64_t k = H.k;
+                const int32_t x = H.row_node[r];
+                const int32_t cx = H.chain_id[x];
+                const int32_t *src = &H.N[(size_t)r * k];
+                cols.resize((size_t)k);
+                for (int64_t q = 0; q < k; ++q) {
+                    const int32_t slot = (q == cx) ? (int32_t)H.chain_base[cx] : src[q];   // own chain: apart
+                    const int32_t y = H.slot_node[slot];
+                    cols[q] = {y < 0 ? -1 : lvl[y], slot + (int32_t)p->slot_off[c]};
+                }
+                std::stable_sort(cols.begin(), cols.end(),
+                                 [](const std::pair<int32_t, int32_t> &a, const std::pair<int32_t, int32_t> &b) {
+                                     return a.first < b.first;
+                                 });
+                int32_t *dst = &Nm[(size_t)moff[i] + (mkp[i] - k)];
+                for (int64_t q = 0; q < k; ++q) dst[q] = cols[q].second;
+                mnode[i] = (int32_t)(x + p->node_off[c]);
+                mslot[i] = (int32_t)(H.node_slot[x] + p->slot_off[c]);
+                mlevel[i] = lvl[x];
             }
-            std::stable_sort(cols.begin(), cols.end(),
-                             [](const std::pair<int32_t, int32_t> &a, const std::pair<int32_t, int32_t> &b) {
-                                 return a.first < b.first;
-                             });
-            int32_t *dst = &Nm[(size_t)moff[i] + (mkp[i] - k)];
-            for (int64_t q = 0; q < k; ++q) dst[q] = cols[q].second;
-            mnode[i] = (int32_t)(x + p->node_off[c]);
-            mslot[i] = (int32_t)(H.node_slot[x] + p->slot_off[c]);
-            mlevel[i] = lvl[x];
-        }
+        });
         if ((st = upload(p, &D.Nm, Nm.data(), Nm.size()))) return st;
         if ((st = upload(p, &D.mob_off, moff.data(), moff.size()))) return st;
         if ((st = upload(p, &D.mob_kp, mkp.data(), mkp.size()))) return st;
@@ -305,6 +328,7 @@ static mz_status run_zeta(const mz_plan *p, int side, mz_dtype dtype, const void
     if ((e = launch_scan(dtype, sa, L.sh, s)) != cudaSuccess) return cuda_fail(e, "chain scan launch");
     mark_event(++g_last_launches, s);
     GatherArgs ga;
+    ga.blocks_per_sm = p->gather_blocks_per_sm;
     ga.Nt = D.Nt;
     ga.tile_off = D.tile_off;
     ga.tile_k = D.tile_k;
@@ -608,6 +632,30 @@ mz_status mz_check(const mz_plan *plan, mz_stream stream) {
         if (e != cudaSuccess) return cuda_fail(e, "status reset");
         set_last_error("a bounded device-side wait ran out");
         return (mz_status)word;
+    }
+    return MZ_OK;
+}
+
+mz_status mz_plan_tune(mz_plan *plan, const mz_tuning *set, mz_tuning *current) {
+    if (!plan) {
+        set_last_error("null plan");
+        return MZ_ERR_INVALID_ARG;
+    }
+    if (set) {
+        if (set->mobius_blocks_per_sm < 0 || set->mobius_blocks_per_sm > 64 || set->gather_blocks_per_sm < 0 ||
+            set->gather_blocks_per_sm > 256) {
+            set_last_error("tuning value out of range");
+            return MZ_ERR_INVALID_ARG;
+        }
+        if (set->mobius_blocks_per_sm) plan->mob_blocks_per_sm = set->mobius_blocks_per_sm;
+        if (set->mobius_pace_ns) plan->mob_pace_ns = set->mobius_pace_ns < 0 ? 0 : set->mobius_pace_ns;
+        if (set->gather_blocks_per_sm) plan->gather_blocks_per_sm = set->gather_blocks_per_sm;
+    }
+    if (current) {
+        std::memset(current, 0, sizeof(*current));
+        current->mobius_blocks_per_sm = plan->mob_blocks_per_sm;
+        current->mobius_pace_ns = plan->mob_pace_ns ? plan->mob_pace_ns : -1;
+        current->gather_blocks_per_sm = plan->gather_blocks_per_sm;
     }
     return MZ_OK;
 }

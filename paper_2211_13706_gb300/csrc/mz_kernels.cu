@@ -612,7 +612,7 @@ template <class Pol>
 static cudaError_t launch_gather_t(const GatherArgs &a, int num_sms, cudaStream_t st) {
     const int warps_per_block = kGatherThreads / 32;
     int64_t blocks = (a.ntiles + warps_per_block - 1) / warps_per_block;
-    blocks = std::min<int64_t>(blocks, (int64_t)num_sms * 32);
+    blocks = std::min<int64_t>(blocks, (int64_t)num_sms * std::max(1, a.blocks_per_sm));
     if (a.B == 1) {
         k_niv_gather<Pol, 1><<<dim3((unsigned)blocks, 1), kGatherThreads, 0, st>>>(a);
     } else if ((a.B & (a.B - 1)) == 0) {

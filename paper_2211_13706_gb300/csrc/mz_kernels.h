@@ -34,6 +34,7 @@ struct ScanArgs {
 };
 
 struct GatherArgs {
+    int32_t blocks_per_sm;    // grid size: resident 256-thread blocks per SM
     const int32_t *Nt;
     const int64_t *tile_off;  // [ntiles] start of each tile in Nt
     const int32_t *tile_k;    // [ntiles] row length of each tile

@@ -28,7 +28,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Poset", "planted_chain_poset", "random_dag_tiny", "boolean_lattice",
+__all__ = ["Poset", "planted_chain_poset", "planted_batch_specs", "random_dag_tiny", "boolean_lattice",
            "divisor_lattice", "chain_poset", "antichain_poset", "paper_example",
            "function_values", "sub_poset"]
 
@@ -106,7 +106,8 @@ def planted_chain_poset(n: int, k: int, seed: int, *, cross_p: float | None = No
             pending = pending[~good]
         ok = tgt >= 0
         x_src, x_dst = u[ok], tgt[ok]
-        key = np.unique(x_src * n + x_dst)
+        key = np.sort(x_src * n + x_dst)                  # sorted unique (same result as np.unique)
+        key = key[np.concatenate([[True], key[1:] != key[:-1]])] if key.size else key
         x_src, x_dst = key // n, key % n
     else:
         x_src = x_dst = np.zeros(0, dtype=np.int64)
@@ -115,6 +116,17 @@ def planted_chain_poset(n: int, k: int, seed: int, *, cross_p: float | None = No
     dst = np.concatenate([c_dst, x_dst]).astype(np.int32)
     return Poset(n=n, src=src, dst=dst, chain_id=chain_id, rank=rank,
                  name=f"planted(n={n},k={k},seed={seed})")
+
+
+def planted_batch_specs(count: int, seed: int, n_range=(1024, 65536), k_range=(4, 256)):
+    """(n, k, seed) of `count` planted posets for a batch workload: n and k log-uniform
+    in their ranges (rounded; k at most n // 2), one seed per poset."""
+    rng = np.random.default_rng(seed)
+    n = np.rint(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1]), count))).astype(np.int64)
+    k = np.rint(np.exp(rng.uniform(np.log(k_range[0]), np.log(k_range[1]), count))).astype(np.int64)
+    k = np.maximum(1, np.minimum(k, n // 2))
+    seeds = rng.integers(0, 2 ** 31 - 1, count)
+    return [(int(a), int(b), int(c)) for a, b, c in zip(n, k, seeds)]
 
 
 def random_dag_tiny(n: int, p: float, seed: int) -> Poset:
