@@ -143,10 +143,10 @@ def test_c1_float(c1, dtype, sched):
 @pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("dtype", [mz.MZ_F64, mz.MZ_F32C])
 def test_c1_float_batched(c1, dtype, sched):
-    """Batched floats (B = 4 and 16): every column within tolerance of the oracle."""
+    """Batched floats (B = 4, 16, 32): sampled columns within tolerance of the oracle."""
     p, Z, mu = c1
     plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=sched)
-    for batch in (4, 16):
+    for batch in (4, 16, 32):
         f = values(p.n, batch, dtype, 21, ("f64" if dtype == mz.MZ_F64 else "f32") + "u")
         got = run(plan, "zeta", f, dtype)
         for b in range(0, batch, 5):
