@@ -340,20 +340,31 @@ def f32c(x):
     return torch.stack([x.float(), torch.zeros_like(x, dtype=torch.float32)])
 
 
+def _apply(plan, name, x):
+    """Runs transform `name` on a float64 tensor (MZ_F64) or a plain float32 tensor
+    (MZ_F32C with a zero lo plane; the hi plane, the result rounded to fp32, is returned)."""
+    import torch
+    x = x.contiguous()
+    if x.dtype == torch.float32:
+        return getattr(plan, name)(torch.stack([x, torch.zeros_like(x)]))[0].contiguous()
+    return getattr(plan, name)(x)
+
+
 def _autograd():
     import torch
 
     class ZetaFn(torch.autograd.Function):
-        """g = Z f; the gradient of a loss L is dL/df = Z^T dL/dg (the dual poset's zeta)."""
+        """g = Z f; the gradient of a loss L is dL/df = Z^T dL/dg (the dual poset's zeta).
+        float64 tensors use MZ_F64; float32 tensors the compensated MZ_F32C path."""
 
         @staticmethod
         def forward(ctx, f, plan):
             ctx.plan = plan
-            return plan.zeta(f.contiguous())
+            return _apply(plan, "zeta", f)
 
         @staticmethod
         def backward(ctx, grad):
-            return ctx.plan.zeta_T(grad.contiguous()), None
+            return _apply(ctx.plan, "zeta_T", grad), None
 
     class MobiusFn(torch.autograd.Function):
         """f = M g; dL/dg = M^T dL/df (the dual poset's Moebius transform)."""
@@ -361,11 +372,11 @@ def _autograd():
         @staticmethod
         def forward(ctx, g, plan):
             ctx.plan = plan
-            return plan.mobius(g.contiguous())
+            return _apply(plan, "mobius", g)
 
         @staticmethod
         def backward(ctx, grad):
-            return ctx.plan.mobius_T(grad.contiguous()), None
+            return _apply(ctx.plan, "mobius_T", grad), None
 
     return ZetaFn, MobiusFn
 
