@@ -371,6 +371,58 @@ def run_batch_workload(mz, wl, posets, steps, warmup, torch, dtypes=("f32c", "f6
     return out
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of the poset a rank runs: ranks hold independent problems (replicas)."""
+    return 1 + rank
+
+
+def reduce_over_ranks(local_ms: float, units_per_rank: int, dist=None, device=None):
+    """(slowest rank's time in ms, whole-job node-values/s): every rank's units over the
+    slowest rank's time. `dist` is torch.distributed or None for one process."""
+    world = 1
+    t = local_ms
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        x = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, units_per_rank * world / (t / 1e3)
+
+
+def time_differentiation(mz, torch, steps=5, warmup=2):
+    """C5: loss = sum(w * Moebius(zeta(f) * h)) on n = 2^20, k = 64 (cross out-degree 3),
+    B = 16, forward and backward (zeta, Moebius, Moebius^T, zeta^T); fp32 (compensated
+    transforms) and fp64. Units: 4 transforms * n * B node-values per step."""
+    p = pg.planted_chain_poset(1 << 20, 64, 5, cross_deg=3)
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, build_transpose=True)
+    out = {"workload": "planted poset n=2^20, k=64, cross out-degree 3, B=16, loss=sum(w*Moebius(zeta(f)*h))"}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        f, w, h = ((torch.rand((p.n, 16), generator=gen, device="cuda", dtype=dt) * 2 - 1) for _ in range(3))
+        f.requires_grad_()
+
+        def step():
+            f.grad = None
+            loss = (w * mz.MobiusFn.apply(mz.ZetaFn.apply(f, plan) * h, plan)).sum()
+            loss.backward()
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_fwd_bwd": round(ms, 3), "value": round(4 * p.n * 16 / (ms / 1e3), 1), "unit": UNIT}
+    plan.check()
+    plan.close()
+    return out
+
+
 def device_arm(args):
     import torch
     import paper_2211_13706_gb300 as mz
@@ -381,9 +433,9 @@ def device_arm(args):
     # batch-workload posets: generated before this process touches the GPU
     batch_posets = None
     if args.workload in BATCH_WORKLOADS:
-        return batch_arm(args, gen_batch_posets(args.workload, 1 + rank))
+        return batch_arm(args, gen_batch_posets(args.workload, rank_seed(rank)))
     if not args.no_variants:
-        batch_posets = gen_batch_posets("c4s", 1 + rank)
+        batch_posets = gen_batch_posets("c4s", rank_seed(rank))
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -391,7 +443,7 @@ def device_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     wl = WORKLOADS[args.workload]
-    p = make_poset(args.workload, 1 + rank)
+    p = make_poset(args.workload, rank_seed(rank))
     t0 = time.perf_counter()
     plan = mz.Plan(p.n, p.src, p.dst, p.chain_id)
     build_s = time.perf_counter() - t0
@@ -410,12 +462,8 @@ def device_arm(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     n, k, B = p.n, info["k"], 1
-    units = 2 * n * B * args.steps * world
-    value = units / (total_ms / 1e3)
+    total_ms, value = reduce_over_ranks(total_ms, 2 * n * B * args.steps, dist, "cuda")
 
     # round-trip sanity on the timed data (Moebius(zeta(f)) = f)
     if args.dtype == "i64":
@@ -468,6 +516,7 @@ def device_arm(args):
                             "kernels_ms": {a: round(b, 5) for a, b in ktv.items()}}
         pa = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
         kta, tot, _, _, _, _ = time_transforms(mz, pa, x, 3, 1, torch, flush, anti=True)
+        variants["differentiation_c5"] = time_differentiation(mz, torch)
         if batch_posets is not None:
             variants["batched_c4s"] = run_batch_workload(mz, "c4s", batch_posets, args.variant_steps // 5 or 3,
                                                          3, torch)
@@ -523,15 +572,12 @@ def batch_arm(args, posets):
                              dtypes=(dk, "f64") if dk != "f64" else ("f64",))
     clocks = sampler.stop()
     main = res[dk]
-    tot_ms = main["ms_per_step"] * main["steps"]
+    tot_ms, value = reduce_over_ranks(main["ms_per_step"] * main["steps"],
+                                      2 * res["n_total"] * res["batch"] * main["steps"], dist, "cuda")
     if dist:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
         dist.destroy_process_group()
     if rank != 0:
         return
-    value = 2 * res["n_total"] * res["batch"] * main["steps"] * world / (tot_ms / 1e3)
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": main["steps"],
             "warmup": args.warmup, "ms_per_step": round(tot_ms / main["steps"], 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dk, "data": "synthetic",
