@@ -394,7 +394,12 @@ __device__ __forceinline__ void load_ids(const int32_t *p, int32_t *id) {
 template <class M, bool ANTI, int G>
 __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
     using T = typename M::T;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // Warps are numbered across blocks first (warp w of block b is warp b + w * gridDim.x),
+    // so consecutive groups of rows, which share a level, go to different SMs; inside a
+    // warp the rows stay consecutive. G lanes per row.
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int64_t tid = gwarp * 32 + lane;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t grp = tid / G, ngrp = nthreads / G;
     const int b0 = (int)(tid % G);
