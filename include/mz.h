@@ -92,7 +92,8 @@ typedef struct {
                                  d levels above the row it just finished, a thread sleeps about
                                  (d - 2) * pace ns, so rows far from the frontier do not load L2
                                  with polls. 0 = default (1000); negative = no pacing */
-    int32_t reserved1;
+    int32_t niv_format;       /* 0: dense niv map (k entries per node) unless k > 512, then sparse
+                                 (only the finite entries, nnz(N) of Sec. 2.4); 1: dense; 2: sparse */
     int64_t spin_limit;       /* bound on polling iterations of every device-side wait; 0 = default (2^22) */
     /* Test hook, 0 = off. v > 0 makes every transform of this plan skip one publication:
        the look-back flag of scan tile v-1 and the y' word of the (v-1)-th row of the
@@ -119,7 +120,7 @@ typedef struct {
     int32_t max_chain;     /* longest chain of the decomposition (q in Sec. 4) */
     int64_t device_bytes;  /* device memory held by the plan (dual included) */
     int32_t components;    /* posets in the plan (1 for mz_build) */
-    int32_t reserved;
+    int32_t sparse;        /* how many of them keep a sparse niv map */
 } mz_plan_info_t;
 /* For a plan of several posets (mz_build_batch) n, k, nnz and edges are totals over
    them and levels, ulevels, levels_T, ulevels_T and max_chain are maxima. */

@@ -121,9 +121,16 @@ static mz_status upload_side(mz_plan *p, int side) {
         for (const HostSide &H : Hs) {
             const int64_t nt = (H.n + kTileRows - 1) / kTileRows;
             for (int64_t t = 0; t < nt; ++t) {
+                // dense: all k columns; sparse: as many as the tile's longest row, padded
+                int32_t kt = H.k;
+                if (H.sparse) {
+                    kt = 1;
+                    for (int64_t r = t * kTileRows; r < std::min<int64_t>(H.n, (t + 1) * kTileRows); ++r)
+                        kt = std::max(kt, H.row_len[r]);
+                }
                 toff.push_back((int64_t)total);
-                tk.push_back(H.k);
-                total += (size_t)H.k * kTileRows;
+                tk.push_back(kt);
+                total += (size_t)kt * kTileRows;
             }
         }
         D.ntiles = (int64_t)toff.size();
@@ -148,8 +155,13 @@ static mz_status upload_side(mz_plan *p, int side) {
                 for (int64_t r = r0; r < r1; ++r) {
                     const int64_t t = tile0[c] + r / kTileRows, lane = r % kTileRows;
                     int32_t *dst = &tiled[(size_t)toff[t] + lane];
-                    const int32_t *row = &H.N[(size_t)r * k];
-                    for (int64_t q = 0; q < k; ++q) dst[q * kTileRows] = row[q] + so;
+                    if (H.sparse) {           // finite entries only; the rest stay slot 0 (a zero slot)
+                        int64_t q = 0;
+                        H.for_row(r, [&](int32_t, int32_t slot) { dst[(q++) * kTileRows] = slot + so; });
+                    } else {
+                        const int32_t *row = &H.N[(size_t)r * k];
+                        for (int64_t q = 0; q < k; ++q) dst[q * kTileRows] = row[q] + so;
+                    }
                     rn[(size_t)t * kTileRows + lane] = (int32_t)(H.row_node[r] + p->node_off[c]);
                 }
             }
@@ -175,11 +187,18 @@ static mz_status upload_side(mz_plan *p, int side) {
         }
         std::vector<int64_t> moff((size_t)D.n);
         std::vector<int32_t> mkp((size_t)D.n), mnode((size_t)D.n), mslot((size_t)D.n), mlevel((size_t)D.n);
+        // A row holds the finite entries of the other chains (the own chain and the
+        // infinite entries add nothing), padded in front to a multiple of 16, at least 16.
+        parallel_for((int64_t)order.size(), [&](int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i) {
+                const HostSide &H = Hs[order[i].first];
+                const int64_t cnt = H.row_count(order[i].second) - 1;   // minus the own chain
+                mkp[i] = (int32_t)std::max<int64_t>(16, (cnt + 15) / 16 * 16);
+            }
+        });
         size_t total = 0;
         for (size_t i = 0; i < order.size(); ++i) {
-            const HostSide &H = Hs[order[i].first];
             moff[i] = (int64_t)total;
-            mkp[i] = (H.k + 15) / 16 * 16;
             total += (size_t)mkp[i];
         }
         std::vector<int32_t> Nm;
@@ -198,22 +217,18 @@ static mz_status upload_side(mz_plan *p, int side) {
                 const int64_t r = order[i].second;
                 const HostSide &H = Hs[c];
                 const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
-                const int64_t k = H.k;
                 const int32_t x = H.row_node[r];
                 const int32_t cx = H.chain_id[x];
-                const int32_t *src = &H.N[(size_t)r * k];
-                cols.resize((size_t)k);
-                for (int64_t q = 0; q < k; ++q) {
-                    const int32_t slot = (q == cx) ? (int32_t)H.chain_base[cx] : src[q];   // own chain: apart
-                    const int32_t y = H.slot_node[slot];
-                    cols[q] = {y < 0 ? -1 : lvl[y], slot + (int32_t)p->slot_off[c]};
-                }
+                cols.clear();
+                H.for_row(r, [&](int32_t ch, int32_t slot) {
+                    if (ch != cx) cols.push_back({lvl[H.slot_node[slot]], slot + (int32_t)p->slot_off[c]});
+                });
                 std::stable_sort(cols.begin(), cols.end(),
                                  [](const std::pair<int32_t, int32_t> &a, const std::pair<int32_t, int32_t> &b) {
                                      return a.first < b.first;
                                  });
-                int32_t *dst = &Nm[(size_t)moff[i] + (mkp[i] - k)];
-                for (int64_t q = 0; q < k; ++q) dst[q] = cols[q].second;
+                int32_t *dst = &Nm[(size_t)moff[i] + (mkp[i] - (int64_t)cols.size())];
+                for (size_t q = 0; q < cols.size(); ++q) dst[q] = cols[q].second;
                 mnode[i] = (int32_t)(x + p->node_off[c]);
                 mslot[i] = (int32_t)(H.node_slot[x] + p->slot_off[c]);
                 mlevel[i] = lvl[x];
@@ -382,7 +397,7 @@ static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const vo
 // the offsets of the union.
 static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, const int64_t *m,
                                   const int32_t *const *src, const int32_t *const *dst,
-                                  const int32_t *const *chain_id, bool dual) {
+                                  const int32_t *const *chain_id, bool dual, int niv_format) {
     p->host[0].resize(count);
     if (dual) p->host[1].resize(count);
     std::vector<mz_status> sts(count, MZ_OK);
@@ -391,10 +406,11 @@ static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, c
         try {
             std::vector<int32_t> s(src[c], src[c] + m[c]), d(dst[c], dst[c] + m[c]);
             const int32_t *cid = chain_id ? chain_id[c] : nullptr;
-            sts[c] = build_host_side(n[c], s, d, cid, p->host[0][c], errs[c]);
+            sts[c] = build_host_side(n[c], s, d, cid, niv_format, p->host[0][c], errs[c]);
             if (sts[c] == MZ_OK && dual) {
                 // the dual poset: every edge flipped, the same chains (a chain of P is a chain of its dual)
-                sts[c] = build_host_side(n[c], d, s, p->host[0][c].chain_id.data(), p->host[1][c], errs[c]);
+                sts[c] = build_host_side(n[c], d, s, p->host[0][c].chain_id.data(), niv_format, p->host[1][c],
+                                         errs[c]);
                 if (sts[c]) errs[c] = "dual: " + errs[c];
             }
         } catch (const std::bad_alloc &) {
@@ -475,7 +491,11 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
         set_last_error("host allocation failed");
         return MZ_ERR_OOM;
     }
-    mz_status st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0);
+    if (o.niv_format < 0 || o.niv_format > 2) {
+        set_last_error("unknown niv_format");
+        return MZ_ERR_INVALID_ARG;
+    }
+    mz_status st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0, o.niv_format);
     if (st) return st;
     p->schedule = o.mobius_schedule;
     p->host_only = o.host_only != 0;
@@ -669,6 +689,7 @@ mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info) {
     info->schedule = plan->schedule;
     info->components = (int32_t)plan->components();
     for (const HostSide &H : plan->host[0]) {
+        info->sparse += H.sparse ? 1 : 0;
         info->nnz += H.nnz;
         info->edges += H.edges;
         info->levels = std::max(info->levels, H.nlevels);
@@ -706,11 +727,10 @@ mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *
             return MZ_ERR_INVALID_ARG;
         }
         int32_t *o = (int32_t *)out;
+        std::fill(o, o + (size_t)n * (size_t)k, -1);
         for (int64_t x = 0; x < n; ++x) {
             const int64_t cx = H.chain_id[x];
-            const int32_t *row = &H.N[(size_t)(H.node_slot[x] - cx - 1) * k];
-            for (int64_t c = 0; c < k; ++c)
-                o[x * k + c] = row[c] == (int32_t)H.chain_base[c] ? -1 : H.slot_node[row[c]];
+            H.for_row(H.node_slot[x] - cx - 1, [&](int32_t c, int32_t slot) { o[x * k + c] = H.slot_node[slot]; });
         }
         return MZ_OK;
     }

@@ -92,7 +92,7 @@ std::vector<int32_t> max_matching(int64_t n, const std::vector<int64_t> &ptr, co
 }  // namespace
 
 mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const std::vector<int32_t> &dst_in,
-                          const int32_t *chain_in, HostSide &H, std::string &err) {
+                          const int32_t *chain_in, int niv_format, HostSide &H, std::string &err) {
     H = HostSide();
     H.n = n;
     const int64_t m = (int64_t)src_in.size();
@@ -213,40 +213,89 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const s
     // The caller's chains are checked here: the element below x on its chain, or the
     // chain's zero slot when x is the bottom, must be exactly the highest element of
     // x's chain reachable through x's children.
-    try {
-        H.N.assign((size_t)n * (size_t)k, 0);
-    } catch (...) {
-        err = "host allocation of the niv map failed";
-        return MZ_ERR_OOM;
-    }
-    std::vector<int32_t> base32(k), cur(k);
+    // Dense form: one k-wide row per node. Sparse form (Sec. 2.4's nnz(N)): only the
+    // finite entries, as (chain, slot) pairs sorted by chain; chosen when k is large.
+    H.sparse = niv_format == 2 || (niv_format == 0 && k > kDenseMaxChains);
+    std::vector<int32_t> base32(k);
     for (int64_t c = 0; c < k; ++c) base32[c] = (int32_t)H.chain_base[c];
     std::vector<int32_t> kids;
-    for (int64_t i = n - 1; i >= 0; --i) {
-        int32_t x = H.topo[i];
-        std::memcpy(cur.data(), base32.data(), sizeof(int32_t) * k);
-        kids.assign(adj.begin() + ptr[x], adj.begin() + ptr[x + 1]);
-        // highest children first: a child already covered adds nothing (G3 pruning)
-        std::sort(kids.begin(), kids.end(), [&](int32_t a, int32_t b) { return pos[a] < pos[b]; });
-        for (int32_t z : kids) {
-            const int32_t cz = H.chain_id[z];
-            if (cur[cz] >= H.node_slot[z]) continue;
-            const int32_t *row = &H.N[(size_t)(H.node_slot[z] - cz - 1) * k];
-            for (int64_t c = 0; c < k; ++c) cur[c] = std::max(cur[c], row[c]);
+    auto bad_chain = [&](int32_t cx, int32_t x) {
+        err = "chain " + std::to_string(cx) + " is not totally ordered at node " + std::to_string(x);
+        return MZ_ERR_BAD_CHAINS;
+    };
+    if (!H.sparse) {
+        try {
+            H.N.assign((size_t)n * (size_t)k, 0);
+        } catch (...) {
+            err = "host allocation of the niv map failed";
+            return MZ_ERR_OOM;
         }
-        const int32_t cx = H.chain_id[x];
-        const int32_t sx = H.node_slot[x];
-        if (cur[cx] != sx - 1) {
-            err = "chain " + std::to_string(cx) + " is not totally ordered at node " + std::to_string(x);
-            return MZ_ERR_BAD_CHAINS;
+        std::vector<int32_t> cur(k);
+        for (int64_t i = n - 1; i >= 0; --i) {
+            int32_t x = H.topo[i];
+            std::memcpy(cur.data(), base32.data(), sizeof(int32_t) * k);
+            kids.assign(adj.begin() + ptr[x], adj.begin() + ptr[x + 1]);
+            // highest children first: a child already covered adds nothing (G3 pruning)
+            std::sort(kids.begin(), kids.end(), [&](int32_t a, int32_t b) { return pos[a] < pos[b]; });
+            for (int32_t z : kids) {
+                const int32_t cz = H.chain_id[z];
+                if (cur[cz] >= H.node_slot[z]) continue;
+                const int32_t *row = &H.N[(size_t)(H.node_slot[z] - cz - 1) * k];
+                for (int64_t c = 0; c < k; ++c) cur[c] = std::max(cur[c], row[c]);
+            }
+            const int32_t cx = H.chain_id[x];
+            const int32_t sx = H.node_slot[x];
+            if (cur[cx] != sx - 1) return bad_chain(cx, x);
+            cur[cx] = sx;
+            std::memcpy(&H.N[(size_t)(sx - cx - 1) * k], cur.data(), sizeof(int32_t) * k);
         }
-        cur[cx] = sx;
-        std::memcpy(&H.N[(size_t)(sx - cx - 1) * k], cur.data(), sizeof(int32_t) * k);
-    }
-    H.nnz = 0;
-    for (int64_t r = 0; r < n; ++r) {
-        const int32_t *row = &H.N[(size_t)r * k];
-        for (int64_t c = 0; c < k; ++c) H.nnz += row[c] != base32[c];
+        H.nnz = 0;
+        for (int64_t r = 0; r < n; ++r) {
+            const int32_t *row = &H.N[(size_t)r * k];
+            for (int64_t c = 0; c < k; ++c) H.nnz += row[c] != base32[c];
+        }
+    } else {
+        // scratch holds the merged row of the node being built; `touched` lists its chains
+        std::vector<int32_t> scratch(base32), touched;
+        H.row_beg.assign(n, 0);
+        H.row_len.assign(n, 0);
+        H.ent_chain.clear();
+        H.ent_slot.clear();
+        for (int64_t i = n - 1; i >= 0; --i) {
+            int32_t x = H.topo[i];
+            touched.clear();
+            kids.assign(adj.begin() + ptr[x], adj.begin() + ptr[x + 1]);
+            std::sort(kids.begin(), kids.end(), [&](int32_t a, int32_t b) { return pos[a] < pos[b]; });
+            for (int32_t z : kids) {
+                const int32_t cz = H.chain_id[z];
+                if (scratch[cz] >= H.node_slot[z]) continue;
+                const int64_t rz = H.node_slot[z] - cz - 1;
+                const int64_t b = H.row_beg[rz], e = b + H.row_len[rz];
+                for (int64_t q = b; q < e; ++q) {
+                    const int32_t c = H.ent_chain[q];
+                    if (scratch[c] == base32[c]) touched.push_back(c);
+                    scratch[c] = std::max(scratch[c], H.ent_slot[q]);
+                }
+            }
+            const int32_t cx = H.chain_id[x];
+            const int32_t sx = H.node_slot[x];
+            if (scratch[cx] != sx - 1) {
+                for (int32_t c : touched) scratch[c] = base32[c];
+                return bad_chain(cx, x);
+            }
+            if (scratch[cx] == base32[cx]) touched.push_back(cx);
+            scratch[cx] = sx;
+            std::sort(touched.begin(), touched.end());
+            const int64_t r = sx - cx - 1;
+            H.row_beg[r] = (int64_t)H.ent_chain.size();
+            H.row_len[r] = (int32_t)touched.size();
+            for (int32_t c : touched) {
+                H.ent_chain.push_back(c);
+                H.ent_slot.push_back(scratch[c]);
+                scratch[c] = base32[c];
+            }
+        }
+        H.nnz = (int64_t)H.ent_chain.size();
     }
 
     // ---- 6. levels
@@ -258,10 +307,10 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const s
         for (int64_t e = ptr[x]; e < ptr[x + 1]; ++e) h = std::max(h, H.level[adj[e]]);
         H.level[x] = h + 1;
         const int32_t cx = H.chain_id[x];
-        const int32_t *row = &H.N[(size_t)(H.node_slot[x] - cx - 1) * k];
         int32_t u = 0;
-        for (int64_t c = 0; c < k; ++c)
-            if (c != cx && row[c] != base32[c]) u = std::max(u, H.ulevel[H.slot_node[row[c]]] + 1);
+        H.for_row(H.node_slot[x] - cx - 1, [&](int32_t c, int32_t slot) {
+            if (c != cx) u = std::max(u, H.ulevel[H.slot_node[slot]] + 1);
+        });
         H.ulevel[x] = u;
     }
     H.nlevels = *std::max_element(H.level.begin(), H.level.end());

@@ -18,6 +18,7 @@ namespace mz {
 // element at slot r + c + 1. Every map entry is a slot index, so the gather
 // needs no branch for infinity.
 constexpr int kTileRows = 32;  // rows per tile of the tiled (column-major within a tile) map
+constexpr int64_t kDenseMaxChains = 512;  // above this many chains the niv map is kept sparse
 
 struct HostSide {
     int64_t n = 0;
@@ -34,7 +35,31 @@ struct HostSide {
     std::vector<int32_t> node_slot;  // [n]
     std::vector<int32_t> slot_node;  // [n + k], -1 at zero slots
     std::vector<int32_t> row_node;   // [n] node of row r
-    std::vector<int32_t> N;          // [n][k] by row, slot indices
+    bool sparse = false;             // niv map stored as finite entries only
+    std::vector<int32_t> N;          // dense: [n][k] by row, slot indices
+    std::vector<int64_t> row_beg;    // sparse: first entry of row r
+    std::vector<int32_t> row_len;    // sparse: number of entries of row r (own chain included)
+    std::vector<int32_t> ent_chain;  // sparse: chain of each entry, sorted within a row
+    std::vector<int32_t> ent_slot;   // sparse: slot of each entry
+
+    // Calls f(chain, slot) for every finite entry of row r (the own chain included).
+    template <class F>
+    void for_row(int64_t r, F f) const {
+        if (sparse) {
+            for (int64_t q = row_beg[r], e = q + row_len[r]; q < e; ++q) f(ent_chain[q], ent_slot[q]);
+        } else {
+            const int32_t *row = &N[(size_t)r * k];
+            for (int64_t c = 0; c < k; ++c)
+                if (row[c] != (int32_t)chain_base[c]) f((int32_t)c, row[c]);
+        }
+    }
+    // Number of finite entries of row r.
+    int64_t row_count(int64_t r) const {
+        if (sparse) return row_len[r];
+        int64_t cnt = 0;
+        for_row(r, [&](int32_t, int32_t) { ++cnt; });
+        return cnt;
+    }
     std::vector<int32_t> level;      // [n] heights, 1 = minimal
     std::vector<int32_t> ulevel;     // [n] 0 = no dependency on another chain
 };
@@ -95,8 +120,9 @@ namespace mz {
 
 // Host build of one side: validates, orders, decomposes into chains, builds
 // the niv map (Thm. 4) and both level structures. chain_in may be null.
+// niv_format: 0 = dense unless k > kDenseMaxChains, 1 = dense, 2 = sparse.
 mz_status build_host_side(int64_t n, const std::vector<int32_t> &src, const std::vector<int32_t> &dst,
-                          const int32_t *chain_in, HostSide &H, std::string &err);
+                          const int32_t *chain_in, int niv_format, HostSide &H, std::string &err);
 
 void set_last_error(const std::string &s);
 

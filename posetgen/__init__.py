@@ -28,7 +28,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Poset", "planted_chain_poset", "planted_batch_specs", "random_dag_tiny", "boolean_lattice",
+__all__ = ["Poset", "planted_chain_poset", "planted_batch_specs", "random_dag_tiny", "er_dag", "boolean_lattice",
            "divisor_lattice", "chain_poset", "antichain_poset", "paper_example",
            "function_values", "sub_poset"]
 
@@ -140,6 +140,25 @@ def random_dag_tiny(n: int, p: float, seed: int) -> Poset:
     src = node_at_rank[iu[keep]].astype(np.int32)
     dst = node_at_rank[iv[keep]].astype(np.int32)
     return Poset(n=n, src=src, dst=dst, rank=rank, name=f"er(n={n},p={p},seed={seed})")
+
+
+def er_dag(n: int, degree: float, seed: int) -> Poset:
+    """The paper's random DAGs (Sec. 5): Erdos-Renyi on a random order, an ordered pair
+    (earlier, later) is an edge with probability degree / (n - 1), so the average total
+    degree is `degree`. Sampled as the binomial number of edges drawn uniformly (pairs
+    drawn twice are merged)."""
+    rng = np.random.default_rng(seed)
+    m = int(rng.binomial(n * (n - 1) // 2, min(1.0, degree / max(1, n - 1))))
+    a = rng.integers(0, n, size=2 * m + 16)
+    b = rng.integers(0, n, size=2 * m + 16)
+    keep = a < b
+    a, b = a[keep][:m], b[keep][:m]
+    key = np.sort(a.astype(np.int64) * n + b)
+    key = key[np.concatenate([[True], key[1:] != key[:-1]])] if key.size else key
+    a, b = key // n, key % n
+    perm = rng.permutation(n)                              # node ids in a random order
+    return Poset(n=n, src=perm[a].astype(np.int32), dst=perm[b].astype(np.int32),
+                 name=f"er(n={n},deg={degree},seed={seed})")
 
 
 def boolean_lattice(m: int) -> Poset:
