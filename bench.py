@@ -50,6 +50,12 @@ WORKLOADS = {
                desc="planted poset n=2^20, k=64 chains of 16384, cross-chain out-degree 3"),
     "c3": dict(n=1 << 22, k=128, cross_deg=2,
                desc="planted poset n=2^22, k=128 chains of 32768, cross-chain out-degree 2"),
+    # the paper's own random DAGs (Sec. 5): Erdos-Renyi, average degree 4 or 6, chains by
+    # Alg. 1's path cover (k ~ 0.3 n, so the niv map is kept sparse)
+    "er1m4": dict(n=1 << 20, er_degree=4, desc="Erdos-Renyi DAG n=2^20, average degree 4, path-cover chains"),
+    "er1m6": dict(n=1 << 20, er_degree=6, desc="Erdos-Renyi DAG n=2^20, average degree 6, path-cover chains"),
+    "er9m4": dict(n=9_000_000, er_degree=4, desc="Erdos-Renyi DAG n=9e6, average degree 4, path-cover chains"),
+    "er9m6": dict(n=9_000_000, er_degree=6, desc="Erdos-Renyi DAG n=9e6, average degree 6, path-cover chains"),
 }
 BATCH_WORKLOADS = {
     "c4": dict(count=4096, batch=32, cross_deg=2,
@@ -65,8 +71,41 @@ DTYPES = {"f64": ("f64u", "fp64 uniform [-1,1]"), "i64": ("i64:1048576", "int64 
 
 def make_poset(wl: str, seed: int):
     w = WORKLOADS[wl]
+    if "er_degree" in w:
+        return pg.er_dag(w["n"], w["er_degree"], seed)
     kw = {"cross_p": w["cross_p"]} if "cross_p" in w else {"cross_deg": w["cross_deg"]}
     return pg.planted_chain_poset(w["n"], w["k"], seed, **kw)
+
+
+def time_single(mz, torch, wl: str, dtype_key: str, steps: int = 10, seed: int = 1):
+    """zeta + Moebius of one function on one poset (a variant line): build time, per-transform
+    times and node-values/s, and the shape of the plan."""
+    p = make_poset(wl, seed)
+    t0 = time.perf_counter()
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id)
+    build_s = time.perf_counter() - t0
+    kind = DTYPES[dtype_key][0]
+    x = to_dev(pg.function_values(p.n, 1, kind, 2)[:, 0], dtype_key, torch)
+    g = plan.zeta(x)
+    y = plan.mobius(g)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    for _ in range(steps):
+        plan.zeta(x, out=g)
+    e[1].record()
+    for _ in range(steps):
+        plan.mobius(g, out=y)
+    e[2].record()
+    e[2].synchronize()
+    plan.check()
+    tz, tm = e[0].elapsed_time(e[1]) / steps, e[1].elapsed_time(e[2]) / steps
+    info = plan.info
+    plan.close()
+    return {"workload": WORKLOADS[wl]["desc"], "dtype": dtype_key, "n": p.n, "k": info["k"],
+            "nnz": info["nnz"], "ulevels": info["ulevels"], "sparse_map": bool(info["sparse"]),
+            "host_build_s": round(build_s, 2), "zeta_ms": round(tz, 4), "mobius_ms": round(tm, 4),
+            "value": round(2 * p.n / ((tz + tm) / 1e3), 1), "unit": UNIT}
 
 
 def load_peaks():
@@ -161,17 +200,18 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- device arm
-def algorithmic_bytes(kernel: str, n: int, k: int, B: int) -> int:
-    """Bytes a launch must move (the design doc lists them): maps, inputs, outputs; the
-    prefix array y' counts only where it is written or read as an input/output."""
+def algorithmic_bytes(kernel: str, n: int, k: int, B: int, nnz: int) -> int:
+    """Bytes a launch must move: the finite entries of the niv map it needs (nnz(N), or
+    nnz(N) - n without the own-chain entries), its inputs and its outputs; the prefix
+    array y' counts only where a kernel writes it or reads it as its own input."""
     if kernel == "chain_scan":
         return 8 * n * B + 4 * (n + k) + 8 * (n + k) * B
     if kernel == "niv_gather":
-        return 4 * n * k + 4 * n + 8 * n * B
+        return 4 * nnz + 4 * n + 8 * n * B
     if kernel == "mob_init":
         return 4 * (n + k) + 8 * (n + k) * B
     if kernel == "mob_wave":
-        return 4 * n * k + 8 * n + 8 * n * B + 8 * n * B
+        return 4 * (nnz - n) + 12 * n + 8 * n * B + 8 * n * B
     if kernel == "mob_diff":
         return 4 * (n + k) + 8 * (n + k) * B + 8 * n * B
     raise KeyError(kernel)
@@ -480,14 +520,14 @@ def device_arm(args):
 
     peak, peak_kind = load_peaks()
     dom = max(kt, key=kt.get)
-    alg = algorithmic_bytes(dom, n, k, B)
+    alg = algorithmic_bytes(dom, n, k, B, info["nnz"])
     achieved = alg / (kt[dom] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": peak_kind,
             "traffic": load_traffic(dom, args.workload, args.dtype), "algorithmic_bytes": alg,
             "mean_launch_ms": round(kt[dom], 5)}
     kernels = {name: {"mean_ms": round(v, 5), "share": round(v / sum(kt.values()), 4),
-                      "alg_GBps": round(algorithmic_bytes(name, n, k, B) / (v / 1e3) / 1e9, 1)}
+                      "alg_GBps": round(algorithmic_bytes(name, n, k, B, info["nnz"]) / (v / 1e3) / 1e9, 1)}
                for name, v in kt.items()}
     # The gather's other roof: one add per gathered term (nnz(N) per launch). In fp64 it is
     # bound by the FP64 pipe: nominal 1.25 TFLOP/s = 0.625e12 adds/s on GB300.
@@ -517,6 +557,8 @@ def device_arm(args):
         pa = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
         kta, tot, _, _, _, _ = time_transforms(mz, pa, x, 3, 1, torch, flush, anti=True)
         variants["differentiation_c5"] = time_differentiation(mz, torch)
+        variants["paper_er_n2^20_deg4"] = time_single(mz, torch, "er1m4", args.dtype)
+        variants["paper_er_n2^20_deg6"] = time_single(mz, torch, "er1m6", args.dtype)
         if batch_posets is not None:
             variants["batched_c4s"] = run_batch_workload(mz, "c4s", batch_posets, args.variant_steps // 5 or 3,
                                                          3, torch)
@@ -624,7 +666,7 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"f64": "f64", "i64": "int64", "f32c": "f64"}[args.dtype], "data": "synthetic",
-            "config": {"workload": wl["desc"] + f"; f {fdesc}; B=1", "n": p.n, "k": wl["k"], "batch": 1},
+            "config": {"workload": wl["desc"] + f"; f {fdesc}; B=1", "n": p.n, "k": wl.get("k"), "batch": 1},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "one exact zeta row per step (BFS reachability + exact sum), single thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
