@@ -104,6 +104,15 @@ typedef struct {
     void *(*dev_alloc)(size_t bytes, void *ctx);
     void (*dev_free)(void *ptr, void *ctx);
     void *alloc_ctx;
+    /* Nonzero: build the niv map on the device. The host still checks the edges, orders
+       the nodes, finds the chains (Alg. 1) and lays out the slots; the recurrence of
+       Thm. 4 (Alg. 2), the levels of U's dependency graph, the tiled map of the zeta
+       gather and the rows of the Moebius schedule are then computed by kernels, every
+       node as soon as its children are done. The plan is the one the host build makes,
+       entry for entry. Needs a dense niv map (k <= 512, niv_format 0 or 1) and a single
+       poset (mz_build), else MZ_ERR_UNSUPPORTED; not with host_only (MZ_ERR_INVALID_ARG).
+       A bounded wait that runs out fails the build with MZ_ERR_TIMEOUT. */
+    int32_t device_build;
 } mz_build_opts;
 
 typedef struct {
@@ -125,7 +134,8 @@ typedef struct {
 /* For a plan of several posets (mz_build_batch) n, k, nnz and edges are totals over
    them and levels, ulevels, levels_T, ulevels_T and max_chain are maxima. */
 
-/* Arrays mz_plan_export can copy out (host memory, no device work). */
+/* Arrays mz_plan_export can copy out (host memory; no device work, except that the
+   niv map of a plan built with device_build is copied back from the device). */
 typedef enum {
     MZ_EXPORT_CHAIN_ID = 0, /* int32[n]: chain of each node, 0 .. k-1 */
     MZ_EXPORT_CHAIN_POS = 1,/* int32[n]: position on its chain, 0 = bottom (smallest element) */
@@ -152,7 +162,8 @@ typedef enum {
  * The host arrays are only read during the call. The plan's device buffers are
  * allocated on the current CUDA device (skipped with opts->host_only). Returns
  * MZ_ERR_INVALID_ARG (sizes, ids out of range), MZ_ERR_CYCLE, MZ_ERR_BAD_CHAINS,
- * MZ_ERR_OOM or MZ_ERR_CUDA; nothing leaks on error.
+ * MZ_ERR_OOM or MZ_ERR_CUDA (with opts->device_build also MZ_ERR_UNSUPPORTED or
+ * MZ_ERR_TIMEOUT); nothing leaks on error.
  */
 mz_status mz_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                    const int32_t *chain_id, const mz_build_opts *opts, mz_plan **out);

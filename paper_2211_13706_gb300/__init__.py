@@ -50,7 +50,8 @@ class _Opts(ctypes.Structure):
                 ("mobius_schedule", ctypes.c_int32), ("mobius_blocks_per_sm", ctypes.c_int32),
                 ("mobius_pace_ns", ctypes.c_int32), ("niv_format", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("debug_withhold", ctypes.c_int64),
-                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
+                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
+                ("device_build", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -120,13 +121,15 @@ def _check(st: int, where: str):
 
 def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, host_only: bool = False,
              mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0,
-             mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0, niv_format: int = 0) -> int:
+             mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0, niv_format: int = 0,
+             device_build: bool = False) -> int:
     """mz_build: returns the plan handle (an integer). Host arrays are int32."""
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
     cid = None if chain_id is None else np.ascontiguousarray(chain_id, dtype=np.int32)
     opts = _Opts(int(build_transpose), int(host_only), int(mobius_schedule), int(mobius_blocks_per_sm),
-                 int(mobius_pace_ns), int(niv_format), int(spin_limit), int(debug_withhold), None, None, None)
+                 int(mobius_pace_ns), int(niv_format), int(spin_limit), int(debug_withhold), None, None, None,
+                 int(device_build))
     out = ctypes.c_void_p()
     st = lib.mz_build(int(n), int(src.size), src.ctypes.data, dst.ctypes.data,
                       None if cid is None else cid.ctypes.data, ctypes.byref(opts), ctypes.byref(out))
@@ -136,7 +139,8 @@ def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, 
 
 def mz_build_batch(posets, *, build_transpose: bool = False, host_only: bool = False,
                    mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0,
-                   mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0, niv_format: int = 0) -> int:
+                   mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0, niv_format: int = 0,
+                   device_build: bool = False) -> int:
     """mz_build_batch: `posets` is a list of (n, src, dst, chain_id or None)."""
     count = len(posets)
     ns = np.array([int(p[0]) for p in posets], dtype=np.int64)
@@ -147,7 +151,8 @@ def mz_build_batch(posets, *, build_transpose: bool = False, host_only: bool = F
     ptr = lambda arrs: (ctypes.c_void_p * count)(*[None if a is None else a.ctypes.data for a in arrs])
     psrc, pdst, pcid = ptr(srcs), ptr(dsts), ptr(cids)
     opts = _Opts(int(build_transpose), int(host_only), int(mobius_schedule), int(mobius_blocks_per_sm),
-                 int(mobius_pace_ns), int(niv_format), int(spin_limit), int(debug_withhold), None, None, None)
+                 int(mobius_pace_ns), int(niv_format), int(spin_limit), int(debug_withhold), None, None, None,
+                 int(device_build))
     out = ctypes.c_void_p()
     st = lib.mz_build_batch(count, ns.ctypes.data, ms.ctypes.data, psrc, pdst,
                             None if all(c is None for c in cids) else pcid, ctypes.byref(opts), ctypes.byref(out))

@@ -1,6 +1,6 @@
 """Builds libmz.so (the C ABI of include/mz.h) in-tree for sm_103a.
 
-Three translation units compiled in parallel, then linked with the CUDA
+Four translation units compiled in parallel, then linked with the CUDA
 runtime statically. Output: paper_2211_13706_gb300/_build/libmz.so.
 """
 from __future__ import annotations
@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["mz_host.cpp", "mz_kernels.cu", "mz_abi.cu"]
+SOURCES = ["mz_host.cpp", "mz_kernels.cu", "mz_build.cu", "mz_abi.cu"]
 
 
 def _nvcc() -> str:

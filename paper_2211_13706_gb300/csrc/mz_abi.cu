@@ -244,6 +244,227 @@ static mz_status upload_side(mz_plan *p, int side) {
     return MZ_OK;
 }
 
+// Device memory held only while a plan is built; freed (after the device is idle)
+// when the build returns, through the caller's allocator if it gave one.
+class BuildScratch {
+  public:
+    explicit BuildScratch(mz_plan *p) : p_(p) {}
+    BuildScratch(const BuildScratch &) = delete;
+    BuildScratch &operator=(const BuildScratch &) = delete;
+    ~BuildScratch() {
+        if (!bufs_.empty()) cudaDeviceSynchronize();
+        for (void *q : bufs_) {
+            if (p_->dev_free) p_->dev_free(q, p_->alloc_ctx);
+            else cudaFree(q);
+        }
+    }
+    template <class T>
+    T *get(size_t count) {
+        void *q = nullptr;
+        const size_t bytes = align256(std::max<size_t>(sizeof(T) * count, 256));
+        if (p_->dev_alloc) {
+            q = p_->dev_alloc(bytes, p_->alloc_ctx);
+        } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            q = nullptr;
+        }
+        if (q) bufs_.push_back(q);
+        return (T *)q;
+    }
+    template <class T>
+    mz_status put(T **dst, const T *src, size_t count) {
+        *dst = get<T>(count);
+        if (!*dst) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        if (count == 0) return MZ_OK;
+        cudaError_t e = cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? MZ_OK : cuda_fail(e, "cudaMemcpy");
+    }
+
+  private:
+    mz_plan *p_;
+    std::vector<void *> bufs_;
+};
+
+// The same layouts as upload_side for a single poset whose niv map is built on the
+// device (mz_build_opts::device_build): the host sends the children lists and the
+// slot layout, the kernels of mz_build.cu build the map, the U levels, the tiles and
+// the Moebius rows, and the host fills in the per-node arrays it keeps (U levels,
+// nnz) and the O(n) orderings in between.
+static mz_status upload_side_device(mz_plan *p, int side) {
+    HostSide &H = p->host[side][0];
+    DeviceSide &D = p->dev[side];
+    const int64_t n = H.n, k = H.k, nslots = n + k;
+    D.n = n;
+    D.nslots = nslots;
+    D.k_max = H.k;
+    D.kpad_max = (H.k + 15) / 16 * 16;
+    mz_status st;
+    cudaError_t e;
+    {   // slot map, padded with -1 to a multiple of 64 entries
+        std::vector<int32_t> sn(((size_t)nslots + 63) / 64 * 64, -1);
+        std::copy(H.slot_node.begin(), H.slot_node.end(), sn.begin());
+        if ((st = upload(p, &D.slot_node, sn.data(), sn.size()))) return st;
+    }
+    BuildScratch tmp(p);
+    // ---- the niv map (Thm. 4), bottom-up by height
+    std::vector<int32_t> order(n), topo_pos(n), base(k);
+    {
+        std::vector<int64_t> cnt((size_t)H.nlevels + 2, 0);
+        for (int64_t x = 0; x < n; ++x) cnt[H.level[x]]++;
+        for (size_t l = 1; l < cnt.size(); ++l) cnt[l] += cnt[l - 1];
+        for (int64_t i = n - 1; i >= 0; --i) order[(size_t)cnt[H.level[H.topo[i]] - 1]++] = H.topo[i];
+        for (int64_t i = 0; i < n; ++i) topo_pos[H.topo[i]] = (int32_t)i;
+        for (int64_t c = 0; c < k; ++c) base[c] = (int32_t)H.chain_base[c];
+    }
+    BuildNivArgs a;
+    std::memset(&a, 0, sizeof(a));
+    int64_t *d_ptr;
+    int32_t *d_adj, *d_order, *d_node_slot, *d_chain, *d_base, *d_pos;
+    if ((st = tmp.put(&d_ptr, H.csr_ptr.data(), H.csr_ptr.size()))) return st;
+    if ((st = tmp.put(&d_adj, H.csr_adj.data(), H.csr_adj.size()))) return st;
+    if ((st = tmp.put(&d_order, order.data(), order.size()))) return st;
+    if ((st = tmp.put(&d_node_slot, H.node_slot.data(), H.node_slot.size()))) return st;
+    if ((st = tmp.put(&d_chain, H.chain_id.data(), H.chain_id.size()))) return st;
+    if ((st = tmp.put(&d_base, base.data(), base.size()))) return st;
+    if ((st = tmp.put(&d_pos, topo_pos.data(), topo_pos.size()))) return st;
+    int32_t *d_N = tmp.get<int32_t>((size_t)n * (size_t)k);
+    int32_t *d_uslot = tmp.get<int32_t>((size_t)nslots);
+    int32_t *d_rowcnt = tmp.get<int32_t>((size_t)n);
+    uint32_t *d_ready = tmp.get<uint32_t>((size_t)n);
+    uint32_t *d_small = tmp.get<uint32_t>(64);   // ticket, status, bad, nnz (8-byte aligned at word 4)
+    if (!d_N || !d_uslot || !d_rowcnt || !d_ready || !d_small) {
+        set_last_error("device allocation failed");
+        return MZ_ERR_OOM;
+    }
+    const uint32_t small_init[6] = {0u, 0u, 0xffffffffu, 0u, 0u, 0u};
+    // the map starts at slot 0 everywhere, so that no read can leave the slot range
+    if ((e = cudaMemset(d_N, 0, sizeof(int32_t) * (size_t)n * (size_t)k)) != cudaSuccess ||
+        (e = cudaMemset(d_uslot, 0xff, sizeof(int32_t) * nslots)) != cudaSuccess ||
+        (e = cudaMemset(d_ready, 0, sizeof(uint32_t) * n)) != cudaSuccess ||
+        (e = cudaMemcpy(d_small, small_init, sizeof(small_init), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "build setup");
+    a.ptr = d_ptr;
+    a.adj = d_adj;
+    a.order = d_order;
+    a.node_slot = d_node_slot;
+    a.chain_id = d_chain;
+    a.base = d_base;
+    a.topo_pos = d_pos;
+    a.n = n;
+    a.k = (int32_t)k;
+    a.N = d_N;
+    a.uslot = d_uslot;
+    a.rowcnt = d_rowcnt;
+    a.ready = d_ready;
+    a.ticket = d_small;
+    a.status = d_small + 1;
+    a.bad = (int32_t *)(d_small + 2);
+    a.nnz = (unsigned long long *)(d_small + 4);
+    a.spin_limit = p->spin_limit;
+    if ((e = launch_build_niv(a, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "niv build launch");
+    uint32_t small[6];
+    if ((e = cudaMemcpy(small, d_small, sizeof(small), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "niv build");
+    if (small[1]) {
+        set_last_error(std::string(side ? "dual: " : "") + "device build: a bounded wait ran out");
+        return MZ_ERR_TIMEOUT;
+    }
+    if ((int32_t)small[2] >= 0) {
+        const int32_t x = H.topo[(int32_t)small[2]];
+        set_last_error(std::string(side ? "dual: " : "") + "chain " + std::to_string(H.chain_id[x]) +
+                       " is not totally ordered at node " + std::to_string(x));
+        return MZ_ERR_BAD_CHAINS;
+    }
+    H.nnz = (int64_t)(small[4] | ((uint64_t)small[5] << 32));
+    std::vector<int32_t> uslot((size_t)nslots), rowcnt((size_t)n);
+    if ((e = cudaMemcpy(uslot.data(), d_uslot, sizeof(int32_t) * nslots, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(rowcnt.data(), d_rowcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    H.ulevel.assign(n, 0);
+    for (int64_t x = 0; x < n; ++x) H.ulevel[x] = uslot[H.node_slot[x]];
+    H.nulevels = *std::max_element(H.ulevel.begin(), H.ulevel.end()) + 1;
+    // ---- tiles of 32 rows for the gather
+    {
+        D.ntiles = (n + kTileRows - 1) / kTileRows;
+        std::vector<int64_t> toff((size_t)D.ntiles);
+        std::vector<int32_t> tk((size_t)D.ntiles, (int32_t)k), rn((size_t)D.ntiles * kTileRows, -1);
+        for (int64_t t = 0; t < D.ntiles; ++t) toff[t] = t * k * kTileRows;
+        std::copy(H.row_node.begin(), H.row_node.end(), rn.begin());
+        D.Nt = (int32_t *)plan_alloc(p, sizeof(int32_t) * (size_t)D.ntiles * kTileRows * (size_t)k);
+        if (!D.Nt) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        if ((e = launch_build_tiles(d_N, n, (int32_t)k, D.Nt, p->num_sms, 0)) != cudaSuccess)
+            return cuda_fail(e, "tile build launch");
+        if ((st = upload(p, &D.tile_off, toff.data(), toff.size()))) return st;
+        if ((st = upload(p, &D.tile_k, tk.data(), tk.size()))) return st;
+        if ((st = upload(p, &D.row_node, rn.data(), rn.size()))) return st;
+    }
+    // ---- Moebius rows, by level of the schedule and then by row
+    {
+        const bool anti = (p->schedule == MZ_SCHED_ANTICHAIN);
+        const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
+        const int32_t maxlvl = anti ? H.nlevels : H.nulevels;
+        std::vector<int64_t> cnt((size_t)maxlvl + 2, 0);
+        for (int64_t r = 0; r < n; ++r) cnt[lvl[H.row_node[r]] + 1]++;
+        for (size_t l = 1; l < cnt.size(); ++l) cnt[l] += cnt[l - 1];
+        std::vector<int32_t> mrow((size_t)n), mkp((size_t)n), mnode((size_t)n), mslot((size_t)n), mlevel((size_t)n);
+        std::vector<int64_t> moff((size_t)n);
+        for (int64_t r = 0; r < n; ++r) mrow[(size_t)cnt[lvl[H.row_node[r]]]++] = (int32_t)r;
+        int64_t total = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t r = mrow[i], x = H.row_node[r];
+            mkp[i] = std::max<int32_t>(16, (rowcnt[r] - 1 + 15) / 16 * 16);
+            moff[i] = total;
+            total += mkp[i];
+            mnode[i] = x;
+            mslot[i] = H.node_slot[x];
+            mlevel[i] = lvl[x];
+        }
+        const int32_t *key_slot = d_uslot;   // U levels by slot, -1 at zero slots
+        if (anti) {
+            std::vector<int32_t> ks((size_t)nslots);
+            for (int64_t s2 = 0; s2 < nslots; ++s2) ks[s2] = H.slot_node[s2] < 0 ? -1 : H.level[H.slot_node[s2]];
+            int32_t *d_ks;
+            if ((st = tmp.put(&d_ks, ks.data(), ks.size()))) return st;
+            key_slot = d_ks;
+        }
+        D.Nm = (int32_t *)plan_alloc(p, sizeof(int32_t) * (size_t)total);
+        if (!D.Nm) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        if ((e = cudaMemset(D.Nm, 0, sizeof(int32_t) * (size_t)total)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemset");
+        if ((st = upload(p, &D.mob_off, moff.data(), moff.size()))) return st;
+        if ((st = upload(p, &D.mob_kp, mkp.data(), mkp.size()))) return st;
+        if ((st = upload(p, &D.mob_node, mnode.data(), mnode.size()))) return st;
+        if ((st = upload(p, &D.mob_slot, mslot.data(), mslot.size()))) return st;
+        if ((st = upload(p, &D.mob_level, mlevel.data(), mlevel.size()))) return st;
+        int32_t *d_mrow;
+        if ((st = tmp.put(&d_mrow, mrow.data(), mrow.size()))) return st;
+        BuildMobArgs b;
+        b.N = d_N;
+        b.k = (int32_t)k;
+        b.mrow = d_mrow;
+        b.moff = D.mob_off;
+        b.mkp = D.mob_kp;
+        b.mslot = D.mob_slot;
+        b.key_slot = key_slot;
+        b.n = n;
+        b.Nm = D.Nm;
+        if ((e = launch_build_mob_rows(b, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "row build launch");
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "device build");
+    H.csr_ptr = std::vector<int64_t>();
+    H.csr_adj = std::vector<int32_t>();
+    return MZ_OK;
+}
+
 // ---------------------------------------------------------------- workspace
 struct WsLayout {
     ScanShape sh;
@@ -397,7 +618,7 @@ static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const vo
 // the offsets of the union.
 static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, const int64_t *m,
                                   const int32_t *const *src, const int32_t *const *dst,
-                                  const int32_t *const *chain_id, bool dual, int niv_format) {
+                                  const int32_t *const *chain_id, bool dual, int niv_format, bool device_niv) {
     p->host[0].resize(count);
     if (dual) p->host[1].resize(count);
     std::vector<mz_status> sts(count, MZ_OK);
@@ -406,11 +627,11 @@ static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, c
         try {
             std::vector<int32_t> s(src[c], src[c] + m[c]), d(dst[c], dst[c] + m[c]);
             const int32_t *cid = chain_id ? chain_id[c] : nullptr;
-            sts[c] = build_host_side(n[c], s, d, cid, niv_format, p->host[0][c], errs[c]);
+            sts[c] = build_host_side(n[c], s, d, cid, niv_format, device_niv, p->host[0][c], errs[c]);
             if (sts[c] == MZ_OK && dual) {
                 // the dual poset: every edge flipped, the same chains (a chain of P is a chain of its dual)
-                sts[c] = build_host_side(n[c], d, s, p->host[0][c].chain_id.data(), niv_format, p->host[1][c],
-                                         errs[c]);
+                sts[c] = build_host_side(n[c], d, s, p->host[0][c].chain_id.data(), niv_format, device_niv,
+                                         p->host[1][c], errs[c]);
                 if (sts[c]) errs[c] = "dual: " + errs[c];
             }
         } catch (const std::bad_alloc &) {
@@ -495,7 +716,16 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
         set_last_error("unknown niv_format");
         return MZ_ERR_INVALID_ARG;
     }
-    mz_status st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0, o.niv_format);
+    if (o.device_build && o.host_only) {
+        set_last_error("device_build needs a device plan (host_only is set)");
+        return MZ_ERR_INVALID_ARG;
+    }
+    if (o.device_build && count != 1) {
+        set_last_error("device_build builds single-poset plans only");
+        return MZ_ERR_UNSUPPORTED;
+    }
+    mz_status st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0, o.niv_format,
+                                    o.device_build != 0);
     if (st) return st;
     p->schedule = o.mobius_schedule;
     p->host_only = o.host_only != 0;
@@ -518,7 +748,8 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
         } else if ((e = cudaMemset(p->d_status, 0, 256)) != cudaSuccess) {
             st = cuda_fail(e, "cudaMemset");
         }
-        for (int side = 0; side < (p->has_dual ? 2 : 1) && st == MZ_OK; ++side) st = upload_side(p.get(), side);
+        for (int side = 0; side < (p->has_dual ? 2 : 1) && st == MZ_OK; ++side)
+            st = p->host[side][0].niv_on_device ? upload_side_device(p.get(), side) : upload_side(p.get(), side);
         if (st) {
             plan_free_all(p.get());
             return st;
@@ -728,6 +959,18 @@ mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *
         }
         int32_t *o = (int32_t *)out;
         std::fill(o, o + (size_t)n * (size_t)k, -1);
+        if (H.niv_on_device) {   // the map exists only on the device: copy the tiles back
+            const DeviceSide &D = plan->dev[dual ? 1 : 0];
+            std::vector<int32_t> t((size_t)D.ntiles * kTileRows * (size_t)k);
+            cudaError_t e = cudaMemcpy(t.data(), D.Nt, sizeof(int32_t) * t.size(), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+            for (int64_t r = 0; r < n; ++r) {
+                const int64_t x = H.row_node[r];
+                const int32_t *col = &t[(size_t)(r / kTileRows) * kTileRows * k + r % kTileRows];
+                for (int64_t c = 0; c < k; ++c) o[x * k + c] = H.slot_node[col[c * kTileRows]];
+            }
+            return MZ_OK;
+        }
         for (int64_t x = 0; x < n; ++x) {
             const int64_t cx = H.chain_id[x];
             H.for_row(H.node_slot[x] - cx - 1, [&](int32_t c, int32_t slot) { o[x * k + c] = H.slot_node[slot]; });

@@ -9,6 +9,8 @@
 //      checked on the way;
 //   6. antichain levels (Alg. 6, heights) and the levels of U's dependency
 //      graph (the schedule of the forward substitution of Alg. 4).
+// With the device build only steps 1-4 and the heights run here; mz_build.cu
+// has the rest.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -92,7 +94,7 @@ std::vector<int32_t> max_matching(int64_t n, const std::vector<int64_t> &ptr, co
 }  // namespace
 
 mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const std::vector<int32_t> &dst_in,
-                          const int32_t *chain_in, int niv_format, HostSide &H, std::string &err) {
+                          const int32_t *chain_in, int niv_format, bool device_niv, HostSide &H, std::string &err) {
     H = HostSide();
     H.n = n;
     const int64_t m = (int64_t)src_in.size();
@@ -207,6 +209,29 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const s
             base += (int64_t)chains[c].size() + 1;
         }
         H.chain_base[k] = base;
+    }
+
+    if (device_niv) {
+        // Steps 5 and the U levels of step 6 run on the device; the host keeps the
+        // children lists for the upload and computes the heights (one pass over the edges).
+        if (niv_format == 2 || k > kDenseMaxChains) {
+            err = "the device build keeps a dense niv map: it needs k <= " + std::to_string(kDenseMaxChains) +
+                  " chains (this poset has " + std::to_string(k) + ") and niv_format 0 or 1";
+            return MZ_ERR_UNSUPPORTED;
+        }
+        H.sparse = false;
+        H.niv_on_device = true;
+        H.level.assign(n, 1);
+        for (int64_t i = n - 1; i >= 0; --i) {
+            const int32_t x = H.topo[i];
+            int32_t h = 0;
+            for (int64_t e = ptr[x]; e < ptr[x + 1]; ++e) h = std::max(h, H.level[adj[e]]);
+            H.level[x] = h + 1;
+        }
+        H.nlevels = *std::max_element(H.level.begin(), H.level.end());
+        H.csr_ptr = std::move(ptr);
+        H.csr_adj = std::move(adj);
+        return MZ_OK;
     }
 
     // ---- 5. niv map by Thm. 4, bottom-up. Entry (x, c) = slot of niv_c(x), or base_c.

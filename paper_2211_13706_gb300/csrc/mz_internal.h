@@ -62,6 +62,11 @@ struct HostSide {
     }
     std::vector<int32_t> level;      // [n] heights, 1 = minimal
     std::vector<int32_t> ulevel;     // [n] 0 = no dependency on another chain
+    // Device build: the niv map exists only on the device (N stays empty, for_row and
+    // row_count must not be called); the children lists are kept until the upload.
+    bool niv_on_device = false;
+    std::vector<int64_t> csr_ptr;    // [n + 1]
+    std::vector<int32_t> csr_adj;    // children of each node, ascending ids
 };
 
 // Device copies of one side (primal or dual) for all components of the plan. The
@@ -121,8 +126,9 @@ namespace mz {
 // Host build of one side: validates, orders, decomposes into chains, builds
 // the niv map (Thm. 4) and both level structures. chain_in may be null.
 // niv_format: 0 = dense unless k > kDenseMaxChains, 1 = dense, 2 = sparse.
+// device_niv: stop after the slot layout and the heights (the device build does the rest).
 mz_status build_host_side(int64_t n, const std::vector<int32_t> &src, const std::vector<int32_t> &dst,
-                          const int32_t *chain_in, int niv_format, HostSide &H, std::string &err);
+                          const int32_t *chain_in, int niv_format, bool device_niv, HostSide &H, std::string &err);
 
 void set_last_error(const std::string &s);
 

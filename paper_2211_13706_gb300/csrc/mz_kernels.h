@@ -1,4 +1,4 @@
-// Launch interface of the CUDA kernels (host side of mz_kernels.cu).
+// Launch interface of the CUDA kernels (host side of mz_kernels.cu and mz_build.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -66,6 +66,44 @@ struct MobArgs {
     int64_t spin_limit;
     int64_t withhold;        // test hook: processing index whose y' is never published (-1: none)
 };
+
+// Device build (mz_build.cu).
+struct BuildNivArgs {
+    const int64_t *ptr;         // [n + 1] children lists (CSR)
+    const int32_t *adj;         // children
+    const int32_t *order;       // [n] nodes bottom-up (ascending height)
+    const int32_t *node_slot;   // [n]
+    const int32_t *chain_id;    // [n]
+    const int32_t *base;        // [k] zero slot of each chain
+    const int32_t *topo_pos;    // [n] position in the host's topological order
+    int64_t n;
+    int32_t k;
+    int32_t *N;                 // [n][k] out: the map, row r = slot - chain - 1
+    int32_t *uslot;             // [n + k] out: U level by slot; -1 preset (stays -1 at zero slots)
+    int32_t *rowcnt;            // [n] out: finite entries of each row, own chain included
+    uint32_t *ready;            // [n] 0 until the node's row is published (zeroed before the launch)
+    uint32_t *ticket;           // claim counter (zeroed)
+    int32_t *bad;               // largest topo_pos of a node whose chain check fails (-1 preset)
+    unsigned long long *nnz;    // total finite entries (zeroed)
+    uint32_t *status;           // MZ_ERR_TIMEOUT after a wait ran out (zeroed)
+    int64_t spin_limit;
+};
+
+struct BuildMobArgs {
+    const int32_t *N;           // [n][k] row-major map
+    int32_t k;
+    const int32_t *mrow;        // [n] row of the i-th row of the schedule
+    const int64_t *moff;        // [n] its start in Nm
+    const int32_t *mkp;         // [n] its padded length
+    const int32_t *mslot;       // [n] slot of its element (the own chain's entry)
+    const int32_t *key_slot;    // [n + k] sort key of the element in each slot, -1 at zero slots
+    int64_t n;
+    int32_t *Nm;                // out, zeroed before the launch
+};
+
+cudaError_t launch_build_niv(const BuildNivArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_build_tiles(const int32_t *N, int64_t n, int32_t k, int32_t *Nt, int num_sms, cudaStream_t st);
+cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream_t st);
 
 ScanShape scan_shape(int64_t nslots, int32_t B);
 void mark_event(int i, cudaStream_t s);   // profiling hook of mz_set_launch_events

@@ -1,0 +1,127 @@
+"""The device build (mz_build_opts::device_build): the niv recurrence of Thm. 4
+(Alg. 2), the U levels, the gather tiles and the Moebius rows computed by
+kernels. The plan must be the host build's, entry for entry: the same exports,
+the same plan info, and bit-identical transforms (same layouts, same order of
+additions). Argument checks run on the CPU; everything else is marked gpu."""
+import numpy as np
+import pytest
+
+import oracle
+import posetgen as pg
+import paper_2211_13706_gb300 as mz
+
+EXPORTS = (mz.MZ_EXPORT_NIV, mz.MZ_EXPORT_LEVEL, mz.MZ_EXPORT_ULEVEL, mz.MZ_EXPORT_CHAIN_ID,
+           mz.MZ_EXPORT_CHAIN_POS, mz.MZ_EXPORT_TOPO)
+INFO_KEYS = ("n", "k", "nnz", "edges", "levels", "ulevels", "levels_T", "ulevels_T", "max_chain", "sparse",
+             "device_bytes")
+
+
+def test_device_build_argument_checks():
+    with pytest.raises(mz.MzError) as e:
+        mz.mz_build(3, [0, 1], [1, 2], device_build=True, host_only=True)
+    assert e.value.status == mz.MZ_ERR_INVALID_ARG
+    p = pg.paper_example()
+    with pytest.raises(mz.MzError) as e:
+        mz.mz_build_batch([(p.n, p.src, p.dst, None)] * 2, device_build=True)
+    assert e.value.status == mz.MZ_ERR_UNSUPPORTED
+    # sparse niv maps stay on the host: refused before any device work
+    with pytest.raises(mz.MzError) as e:
+        mz.mz_build(p.n, p.src, p.dst, device_build=True, niv_format=2)
+    assert e.value.status == mz.MZ_ERR_UNSUPPORTED
+    q = pg.antichain_poset(600)                     # 600 chains > 512
+    with pytest.raises(mz.MzError) as e:
+        mz.mz_build(q.n, q.src, q.dst, device_build=True)
+    assert e.value.status == mz.MZ_ERR_UNSUPPORTED and "512" in str(e.value)
+
+
+def _cases():
+    ex = pg.paper_example()
+    bl = pg.boolean_lattice(8)
+    dl, _ = pg.divisor_lattice(720)
+    pl = pg.planted_chain_poset(4096, 16, 1, cross_p=4 / 4096)
+    pl33 = pg.planted_chain_poset(3000, 33, 2, cross_deg=3)
+    pl300 = pg.planted_chain_poset(6000, 300, 3, cross_deg=2)
+    return [
+        ("paper_example", ex, None),
+        ("boolean_lattice_8", bl, None),
+        ("divisor_lattice_720", dl, None),
+        ("chain_500", pg.chain_poset(500, 1), None),
+        ("antichain_100", pg.antichain_poset(100), None),
+        ("planted_4096_k16", pl, pl.chain_id),
+        ("planted_3000_k33", pl33, pl33.chain_id),
+        ("planted_6000_k300", pl300, pl300.chain_id),
+        ("planted_4096_matching", pl, None),
+        ("er_400_deg3", pg.er_dag(400, 3, 9), None),
+        ("tiny_dag", pg.random_dag_tiny(40, 0.2, 5), None),
+    ]
+
+
+CASES = _cases()
+
+
+def _pair(p, cid, **kw):
+    host = mz.Plan(p.n, p.src, p.dst, cid, **kw)
+    dev = mz.Plan(p.n, p.src, p.dst, cid, device_build=True, **kw)
+    return host, dev
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,p,cid", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("schedule", [mz.MZ_SCHED_ULEVEL, mz.MZ_SCHED_ANTICHAIN])
+def test_device_build_equals_host_build(name, p, cid, schedule):
+    host, dev = _pair(p, cid, build_transpose=True, mobius_schedule=schedule)
+    for key in INFO_KEYS:
+        assert host.info[key] == dev.info[key], key
+    for dual in (False, True):
+        for w in EXPORTS:
+            assert np.array_equal(host.export(w, dual=dual), dev.export(w, dual=dual)), (w, dual)
+    # the map itself against the oracle's niv (independent of both builds)
+    Z = oracle.closure(p.n, p.src, p.dst)
+    chains = dev.export(mz.MZ_EXPORT_CHAIN_ID)
+    assert np.array_equal(dev.export(mz.MZ_EXPORT_NIV), oracle.niv(Z, chains))
+    assert np.array_equal(dev.export(mz.MZ_EXPORT_NIV, dual=True), oracle.niv(np.ascontiguousarray(Z.T), chains))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,p,cid", CASES[:6] + CASES[7:8], ids=[c[0] for c in CASES[:6] + CASES[7:8]])
+def test_device_built_transforms_bit_identical(name, p, cid):
+    import torch
+    host, dev = _pair(p, cid, build_transpose=True)
+    xi = torch.from_numpy(pg.function_values(p.n, 3, "i64:1000", 4)).cuda()
+    xf = torch.from_numpy(pg.function_values(p.n, 3, "f64u", 5)).cuda()
+    for op in ("zeta", "mobius", "zeta_T", "mobius_T"):
+        for x in (xi, xf):
+            a = getattr(host, op)(x)
+            b = getattr(dev, op)(x)
+            host.check()
+            dev.check()
+            assert torch.equal(a, b), op
+    # int64 against the oracle's exact zeta
+    want = oracle.zeta(oracle.closure(p.n, p.src, p.dst), xi.cpu().numpy())
+    assert np.array_equal(dev.zeta(xi).cpu().numpy(), want)
+
+
+@pytest.mark.gpu
+def test_device_build_bad_chains_same_error():
+    p = pg.planted_chain_poset(2000, 8, 4, cross_deg=2)
+    bad = p.chain_id.copy()
+    # move one element to another chain: that chain is no longer totally ordered
+    bad[np.flatnonzero(bad == 0)[len(bad) // 40]] = 1
+    errs = []
+    for device_build in (False, True):
+        with pytest.raises(mz.MzError) as e:
+            mz.mz_build(p.n, p.src, p.dst, bad, device_build=device_build)
+        errs.append((e.value.status, str(e.value).split(":", 1)[-1]))
+    assert errs[0][0] == errs[1][0] == mz.MZ_ERR_BAD_CHAINS
+    assert errs[0][1] == errs[1][1]
+
+
+@pytest.mark.gpu
+def test_device_build_full_size_planted():
+    """n = 2^20, k = 64 chains of 16384: the maps, levels and nnz equal the host build's."""
+    p = pg.planted_chain_poset(1 << 20, 64, 1)
+    host, dev = _pair(p, p.chain_id)
+    for key in INFO_KEYS:
+        assert host.info[key] == dev.info[key], key
+    for w in (mz.MZ_EXPORT_NIV, mz.MZ_EXPORT_ULEVEL):
+        assert np.array_equal(host.export(w), dev.export(w)), w
