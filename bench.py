@@ -554,6 +554,16 @@ def device_arm(args):
             variants[vd] = {"value": 2 * n * args.variant_steps / (tot / 1e3),
                             "ms_per_step": tot / args.variant_steps,
                             "kernels_ms": {a: round(b, 5) for a, b in ktv.items()}}
+        if not info["sparse"]:
+            # the same plan built by the device build (Thm. 4's recurrence, U levels and
+            # layouts in kernels); outside any timed region
+            t0 = time.perf_counter()
+            pd = mz.Plan(p.n, p.src, p.dst, p.chain_id, device_build=True)
+            dev_s = time.perf_counter() - t0
+            same = all(pd.info[key] == info[key] for key in ("nnz", "levels", "ulevels", "device_bytes")) and \
+                np.array_equal(pd.export(mz.MZ_EXPORT_ULEVEL), plan.export(mz.MZ_EXPORT_ULEVEL))
+            variants["plan_build"] = {"host_s": round(build_s, 3), "device_s": round(dev_s, 3), "same_plan": bool(same)}
+            pd.close()
         pa = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
         kta, tot, _, _, _, _ = time_transforms(mz, pa, x, 3, 1, torch, flush, anti=True)
         variants["differentiation_c5"] = time_differentiation(mz, torch)
