@@ -105,13 +105,15 @@ typedef struct {
     void (*dev_free)(void *ptr, void *ctx);
     void *alloc_ctx;
     /* Nonzero: build the niv map on the device. The host still checks the edges, orders
-       the nodes, finds the chains (Alg. 1) and lays out the slots; the recurrence of
-       Thm. 4 (Alg. 2), the levels of U's dependency graph, the tiled map of the zeta
-       gather and the rows of the Moebius schedule are then computed by kernels, every
-       node as soon as its children are done. The plan is the one the host build makes,
-       entry for entry. Needs a dense niv map (k <= 512, niv_format 0 or 1) and a single
-       poset (mz_build), else MZ_ERR_UNSUPPORTED; not with host_only (MZ_ERR_INVALID_ARG).
-       A bounded wait that runs out fails the build with MZ_ERR_TIMEOUT. */
+       the nodes, finds the chains (Alg. 1), lays out the slots and computes the heights;
+       the recurrence of Thm. 4 (Alg. 2), the levels of U's dependency graph, the tiled
+       map of the zeta gather and the rows of the Moebius schedule are then computed by
+       kernels: for a dense map every node as soon as its children are done, for a sparse
+       map one height level after the other. The plan is the one the host build makes,
+       entry for entry. Single posets only (mz_build; mz_build_batch returns
+       MZ_ERR_UNSUPPORTED), a dense map only with k <= 512 (niv_format 1 with more chains:
+       MZ_ERR_UNSUPPORTED); not with host_only (MZ_ERR_INVALID_ARG). A bounded wait that
+       runs out fails the build with MZ_ERR_TIMEOUT. */
     int32_t device_build;
 } mz_build_opts;
 

@@ -11,6 +11,7 @@
 #include <thread>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mz_internal.h"
@@ -271,6 +272,15 @@ class BuildScratch {
         if (q) bufs_.push_back(q);
         return (T *)q;
     }
+    // Frees one buffer before the build ends (after the device is idle).
+    void release(void *q) {
+        auto it = std::find(bufs_.begin(), bufs_.end(), q);
+        if (it == bufs_.end()) return;
+        cudaDeviceSynchronize();
+        if (p_->dev_free) p_->dev_free(q, p_->alloc_ctx);
+        else cudaFree(q);
+        bufs_.erase(it);
+    }
     template <class T>
     mz_status put(T **dst, const T *src, size_t count) {
         *dst = get<T>(count);
@@ -292,11 +302,13 @@ class BuildScratch {
 // device (mz_build_opts::device_build): the host sends the children lists and the
 // slot layout, the kernels of mz_build.cu build the map, the U levels, the tiles and
 // the Moebius rows, and the host fills in the per-node arrays it keeps (U levels,
-// nnz) and the O(n) orderings in between.
+// nnz) and the O(n) orderings in between. Dense map: one dataflow launch over all
+// nodes. Sparse map: one launch pair per height level.
 static mz_status upload_side_device(mz_plan *p, int side) {
     HostSide &H = p->host[side][0];
     DeviceSide &D = p->dev[side];
     const int64_t n = H.n, k = H.k, nslots = n + k;
+    const std::string who = side ? "dual: " : "";
     D.n = n;
     D.nslots = nslots;
     D.k_max = H.k;
@@ -309,18 +321,17 @@ static mz_status upload_side_device(mz_plan *p, int side) {
         if ((st = upload(p, &D.slot_node, sn.data(), sn.size()))) return st;
     }
     BuildScratch tmp(p);
-    // ---- the niv map (Thm. 4), bottom-up by height
+    // ---- inputs of the recurrence: nodes bottom-up by height
     std::vector<int32_t> order(n), topo_pos(n), base(k);
+    std::vector<int64_t> level_start((size_t)H.nlevels + 2, 0);
     {
-        std::vector<int64_t> cnt((size_t)H.nlevels + 2, 0);
-        for (int64_t x = 0; x < n; ++x) cnt[H.level[x]]++;
-        for (size_t l = 1; l < cnt.size(); ++l) cnt[l] += cnt[l - 1];
-        for (int64_t i = n - 1; i >= 0; --i) order[(size_t)cnt[H.level[H.topo[i]] - 1]++] = H.topo[i];
+        for (int64_t x = 0; x < n; ++x) level_start[H.level[x]]++;
+        for (size_t l = 1; l < level_start.size(); ++l) level_start[l] += level_start[l - 1];
+        std::vector<int64_t> fill(level_start);
+        for (int64_t i = n - 1; i >= 0; --i) order[(size_t)fill[H.level[H.topo[i]] - 1]++] = H.topo[i];
         for (int64_t i = 0; i < n; ++i) topo_pos[H.topo[i]] = (int32_t)i;
         for (int64_t c = 0; c < k; ++c) base[c] = (int32_t)H.chain_base[c];
     }
-    BuildNivArgs a;
-    std::memset(&a, 0, sizeof(a));
     int64_t *d_ptr;
     int32_t *d_adj, *d_order, *d_node_slot, *d_chain, *d_base, *d_pos;
     if ((st = tmp.put(&d_ptr, H.csr_ptr.data(), H.csr_ptr.size()))) return st;
@@ -330,53 +341,148 @@ static mz_status upload_side_device(mz_plan *p, int side) {
     if ((st = tmp.put(&d_chain, H.chain_id.data(), H.chain_id.size()))) return st;
     if ((st = tmp.put(&d_base, base.data(), base.size()))) return st;
     if ((st = tmp.put(&d_pos, topo_pos.data(), topo_pos.size()))) return st;
-    int32_t *d_N = tmp.get<int32_t>((size_t)n * (size_t)k);
     int32_t *d_uslot = tmp.get<int32_t>((size_t)nslots);
     int32_t *d_rowcnt = tmp.get<int32_t>((size_t)n);
-    uint32_t *d_ready = tmp.get<uint32_t>((size_t)n);
-    uint32_t *d_small = tmp.get<uint32_t>(64);   // ticket, status, bad, nnz (8-byte aligned at word 4)
-    if (!d_N || !d_uslot || !d_rowcnt || !d_ready || !d_small) {
+    uint32_t *d_small = tmp.get<uint32_t>(64);   // ticket, status, bad, -, nnz / pool top (u64 at word 4)
+    if (!d_uslot || !d_rowcnt || !d_small) {
         set_last_error("device allocation failed");
         return MZ_ERR_OOM;
     }
     const uint32_t small_init[6] = {0u, 0u, 0xffffffffu, 0u, 0u, 0u};
-    // the map starts at slot 0 everywhere, so that no read can leave the slot range
-    if ((e = cudaMemset(d_N, 0, sizeof(int32_t) * (size_t)n * (size_t)k)) != cudaSuccess ||
-        (e = cudaMemset(d_uslot, 0xff, sizeof(int32_t) * nslots)) != cudaSuccess ||
-        (e = cudaMemset(d_ready, 0, sizeof(uint32_t) * n)) != cudaSuccess ||
+    if ((e = cudaMemset(d_uslot, 0xff, sizeof(int32_t) * nslots)) != cudaSuccess ||
         (e = cudaMemcpy(d_small, small_init, sizeof(small_init), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "build setup");
-    a.ptr = d_ptr;
-    a.adj = d_adj;
-    a.order = d_order;
-    a.node_slot = d_node_slot;
-    a.chain_id = d_chain;
-    a.base = d_base;
-    a.topo_pos = d_pos;
-    a.n = n;
-    a.k = (int32_t)k;
-    a.N = d_N;
-    a.uslot = d_uslot;
-    a.rowcnt = d_rowcnt;
-    a.ready = d_ready;
-    a.ticket = d_small;
-    a.status = d_small + 1;
-    a.bad = (int32_t *)(d_small + 2);
-    a.nnz = (unsigned long long *)(d_small + 4);
-    a.spin_limit = p->spin_limit;
-    if ((e = launch_build_niv(a, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "niv build launch");
+    unsigned long long *d_top = (unsigned long long *)(d_small + 4);
+    auto read_small = [&](uint32_t *out6) -> mz_status {
+        cudaError_t e2 = cudaMemcpy(out6, d_small, 6 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        return e2 == cudaSuccess ? MZ_OK : cuda_fail(e2, "niv build");
+    };
+    auto check_small = [&](const uint32_t *sm) -> mz_status {
+        if (sm[1] == MZ_ERR_OOM) {
+            set_last_error(who + "device build: the row pool overflowed");
+            return MZ_ERR_OOM;
+        }
+        if (sm[1]) {
+            set_last_error(who + "device build: a bounded wait ran out");
+            return MZ_ERR_TIMEOUT;
+        }
+        if ((int32_t)sm[2] >= 0) {
+            const int32_t x = H.topo[(int32_t)sm[2]];
+            set_last_error(who + "chain " + std::to_string(H.chain_id[x]) + " is not totally ordered at node " +
+                           std::to_string(x));
+            return MZ_ERR_BAD_CHAINS;
+        }
+        return MZ_OK;
+    };
     uint32_t small[6];
-    if ((e = cudaMemcpy(small, d_small, sizeof(small), cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return cuda_fail(e, "niv build");
-    if (small[1]) {
-        set_last_error(std::string(side ? "dual: " : "") + "device build: a bounded wait ran out");
-        return MZ_ERR_TIMEOUT;
-    }
-    if ((int32_t)small[2] >= 0) {
-        const int32_t x = H.topo[(int32_t)small[2]];
-        set_last_error(std::string(side ? "dual: " : "") + "chain " + std::to_string(H.chain_id[x]) +
-                       " is not totally ordered at node " + std::to_string(x));
-        return MZ_ERR_BAD_CHAINS;
+    int32_t *d_N = nullptr;                 // dense: [n][k]
+    int64_t *d_row_beg = nullptr;           // sparse: rows in the pool
+    int32_t *d_pool = nullptr;
+    if (!H.sparse) {
+        // ---- dense map: Thm. 4 as a dataflow over all nodes
+        d_N = tmp.get<int32_t>((size_t)n * (size_t)k);
+        uint32_t *d_ready = tmp.get<uint32_t>((size_t)n);
+        if (!d_N || !d_ready) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        // the map starts at slot 0 everywhere, so that no read can leave the slot range
+        if ((e = cudaMemset(d_N, 0, sizeof(int32_t) * (size_t)n * (size_t)k)) != cudaSuccess ||
+            (e = cudaMemset(d_ready, 0, sizeof(uint32_t) * n)) != cudaSuccess)
+            return cuda_fail(e, "build setup");
+        BuildNivArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.ptr = d_ptr;
+        a.adj = d_adj;
+        a.order = d_order;
+        a.node_slot = d_node_slot;
+        a.chain_id = d_chain;
+        a.base = d_base;
+        a.topo_pos = d_pos;
+        a.n = n;
+        a.k = (int32_t)k;
+        a.N = d_N;
+        a.uslot = d_uslot;
+        a.rowcnt = d_rowcnt;
+        a.ready = d_ready;
+        a.ticket = d_small;
+        a.status = d_small + 1;
+        a.bad = (int32_t *)(d_small + 2);
+        a.nnz = d_top;
+        a.spin_limit = p->spin_limit;
+        if ((e = launch_build_niv(a, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "niv build launch");
+        if ((st = read_small(small)) || (st = check_small(small))) return st;
+    } else {
+        // ---- sparse map: one height level per launch pair
+        std::vector<int32_t> slot_chain((size_t)nslots);
+        for (int64_t c = 0; c < k; ++c)
+            for (int64_t q = H.chain_base[c]; q < H.chain_base[c + 1]; ++q) slot_chain[q] = (int32_t)c;
+        int32_t *d_slot_chain;
+        if ((st = tmp.put(&d_slot_chain, slot_chain.data(), slot_chain.size()))) return st;
+        d_row_beg = tmp.get<int64_t>((size_t)n);
+        int64_t *d_cand_off = tmp.get<int64_t>((size_t)n + 1);
+        if (!d_row_beg || !d_cand_off) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        int64_t pool_cap = 0, cand_cap = 0;
+        unsigned long long *d_cand = nullptr;
+        // grows a scratch buffer of the build; `keep` entries of the old one are copied over
+        auto grow = [&](auto *&buf, int64_t &cap, int64_t need, int64_t keep) -> mz_status {
+            if (need <= cap) return MZ_OK;
+            using T = std::remove_reference_t<decltype(*buf)>;
+            const int64_t ncap = std::max<int64_t>(need, cap + cap / 2);
+            T *nb = tmp.get<T>((size_t)ncap);
+            if (!nb) {
+                set_last_error("device allocation failed");
+                return MZ_ERR_OOM;
+            }
+            if (keep > 0) {
+                cudaError_t e2 = cudaMemcpy(nb, buf, sizeof(T) * (size_t)keep, cudaMemcpyDeviceToDevice);
+                if (e2 != cudaSuccess) return cuda_fail(e2, "cudaMemcpy");
+            }
+            if (buf) tmp.release(buf);
+            buf = nb;
+            cap = ncap;
+            return MZ_OK;
+        };
+        if ((st = grow(d_pool, pool_cap, 4 * n + 1024, 0))) return st;
+        SparseLevelArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.ptr = d_ptr;
+        a.adj = d_adj;
+        a.order = d_order;
+        a.node_slot = d_node_slot;
+        a.chain_id = d_chain;
+        a.slot_chain = d_slot_chain;
+        a.base = d_base;
+        a.topo_pos = d_pos;
+        a.row_beg = d_row_beg;
+        a.row_len = d_rowcnt;
+        a.pool_top = d_top;
+        a.cand_off = d_cand_off;
+        a.uslot = d_uslot;
+        a.bad = (int32_t *)(d_small + 2);
+        a.status = d_small + 1;
+        for (int32_t h = 1; h <= H.nlevels; ++h) {
+            a.lo = level_start[h - 1];
+            a.cnt = level_start[h] - a.lo;
+            if (a.cnt == 0) continue;
+            if ((e = launch_sparse_bounds(a, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "sparse build launch");
+            int64_t total = 0;
+            if ((e = cudaMemcpy(&total, d_cand_off + a.cnt, sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return cuda_fail(e, "sparse build");
+            if ((st = read_small(small))) return st;
+            const int64_t top = (int64_t)(small[4] | ((uint64_t)small[5] << 32));
+            // every kept entry comes from a candidate: the level adds at most `total` entries
+            if ((st = grow(d_cand, cand_cap, total, 0))) return st;
+            if ((st = grow(d_pool, pool_cap, top + total, top))) return st;
+            a.cand = d_cand;
+            a.pool = d_pool;
+            a.pool_cap = pool_cap;
+            if ((e = launch_sparse_merge(a, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "sparse build launch");
+        }
+        if ((st = read_small(small)) || (st = check_small(small))) return st;
     }
     H.nnz = (int64_t)(small[4] | ((uint64_t)small[5] << 32));
     std::vector<int32_t> uslot((size_t)nslots), rowcnt((size_t)n);
@@ -391,18 +497,30 @@ static mz_status upload_side_device(mz_plan *p, int side) {
         D.ntiles = (n + kTileRows - 1) / kTileRows;
         std::vector<int64_t> toff((size_t)D.ntiles);
         std::vector<int32_t> tk((size_t)D.ntiles, (int32_t)k), rn((size_t)D.ntiles * kTileRows, -1);
-        for (int64_t t = 0; t < D.ntiles; ++t) toff[t] = t * k * kTileRows;
+        int64_t total = 0;
+        for (int64_t t = 0; t < D.ntiles; ++t) {
+            if (H.sparse) {   // as many columns as the tile's longest row
+                int32_t kt = 1;
+                for (int64_t r = t * kTileRows; r < std::min<int64_t>(n, (t + 1) * kTileRows); ++r)
+                    kt = std::max(kt, rowcnt[r]);
+                tk[t] = kt;
+            }
+            toff[t] = total;
+            total += (int64_t)tk[t] * kTileRows;
+        }
         std::copy(H.row_node.begin(), H.row_node.end(), rn.begin());
-        D.Nt = (int32_t *)plan_alloc(p, sizeof(int32_t) * (size_t)D.ntiles * kTileRows * (size_t)k);
+        D.Nt = (int32_t *)plan_alloc(p, sizeof(int32_t) * (size_t)total);
         if (!D.Nt) {
             set_last_error("device allocation failed");
             return MZ_ERR_OOM;
         }
-        if ((e = launch_build_tiles(d_N, n, (int32_t)k, D.Nt, p->num_sms, 0)) != cudaSuccess)
-            return cuda_fail(e, "tile build launch");
         if ((st = upload(p, &D.tile_off, toff.data(), toff.size()))) return st;
         if ((st = upload(p, &D.tile_k, tk.data(), tk.size()))) return st;
         if ((st = upload(p, &D.row_node, rn.data(), rn.size()))) return st;
+        e = H.sparse ? launch_build_tiles_sparse(d_row_beg, d_rowcnt, d_pool, n, D.ntiles, D.tile_off, D.tile_k, D.Nt,
+                                                 p->num_sms, 0)
+                     : launch_build_tiles(d_N, n, (int32_t)k, D.Nt, p->num_sms, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "tile build launch");
     }
     // ---- Moebius rows, by level of the schedule and then by row
     {
@@ -447,17 +565,33 @@ static mz_status upload_side_device(mz_plan *p, int side) {
         if ((st = upload(p, &D.mob_level, mlevel.data(), mlevel.size()))) return st;
         int32_t *d_mrow;
         if ((st = tmp.put(&d_mrow, mrow.data(), mrow.size()))) return st;
-        BuildMobArgs b;
-        b.N = d_N;
-        b.k = (int32_t)k;
-        b.mrow = d_mrow;
-        b.moff = D.mob_off;
-        b.mkp = D.mob_kp;
-        b.mslot = D.mob_slot;
-        b.key_slot = key_slot;
-        b.n = n;
-        b.Nm = D.Nm;
-        if ((e = launch_build_mob_rows(b, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "row build launch");
+        if (!H.sparse) {
+            BuildMobArgs b;
+            b.N = d_N;
+            b.k = (int32_t)k;
+            b.mrow = d_mrow;
+            b.moff = D.mob_off;
+            b.mkp = D.mob_kp;
+            b.mslot = D.mob_slot;
+            b.key_slot = key_slot;
+            b.n = n;
+            b.Nm = D.Nm;
+            e = launch_build_mob_rows(b, p->num_sms, 0);
+        } else {
+            BuildMobSparseArgs b;
+            b.row_beg = d_row_beg;
+            b.row_len = d_rowcnt;
+            b.pool = d_pool;
+            b.mrow = d_mrow;
+            b.moff = D.mob_off;
+            b.mkp = D.mob_kp;
+            b.mslot = D.mob_slot;
+            b.key_slot = key_slot;
+            b.n = n;
+            b.Nm = D.Nm;
+            e = launch_build_mob_rows_sparse(b, p->num_sms, 0);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "row build launch");
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "device build");
     H.csr_ptr = std::vector<int64_t>();
@@ -959,15 +1093,27 @@ mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *
         }
         int32_t *o = (int32_t *)out;
         std::fill(o, o + (size_t)n * (size_t)k, -1);
-        if (H.niv_on_device) {   // the map exists only on the device: copy the tiles back
+        if (H.niv_on_device) {   // the map exists only on the device: read the gather's tiles back
             const DeviceSide &D = plan->dev[dual ? 1 : 0];
-            std::vector<int32_t> t((size_t)D.ntiles * kTileRows * (size_t)k);
-            cudaError_t e = cudaMemcpy(t.data(), D.Nt, sizeof(int32_t) * t.size(), cudaMemcpyDeviceToHost);
+            std::vector<int64_t> toff((size_t)D.ntiles);
+            std::vector<int32_t> tk((size_t)D.ntiles);
+            cudaError_t e = cudaMemcpy(toff.data(), D.tile_off, sizeof(int64_t) * toff.size(), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(tk.data(), D.tile_k, sizeof(int32_t) * tk.size(), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+            const size_t total = D.ntiles ? (size_t)toff.back() + (size_t)tk.back() * kTileRows : 0;
+            std::vector<int32_t> t(total);
+            if ((e = cudaMemcpy(t.data(), D.Nt, sizeof(int32_t) * total, cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return cuda_fail(e, "cudaMemcpy");
+            // a tile row lists slots (every chain in order for a dense map, the finite
+            // entries for a sparse one); zero slots stand for infinity
             for (int64_t r = 0; r < n; ++r) {
-                const int64_t x = H.row_node[r];
-                const int32_t *col = &t[(size_t)(r / kTileRows) * kTileRows * k + r % kTileRows];
-                for (int64_t c = 0; c < k; ++c) o[x * k + c] = H.slot_node[col[c * kTileRows]];
+                const int64_t x = H.row_node[r], tt = r / kTileRows;
+                const int32_t *col = &t[(size_t)toff[tt] + r % kTileRows];
+                for (int64_t q = 0; q < tk[tt]; ++q) {
+                    const int32_t y = H.slot_node[col[q * kTileRows]];
+                    if (y >= 0) o[x * k + H.chain_id[y]] = y;
+                }
             }
             return MZ_OK;
         }

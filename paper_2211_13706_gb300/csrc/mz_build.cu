@@ -221,6 +221,207 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_mob_rows(BuildMobArgs a
     }
 }
 
+// ---------------------------------------------------------------- sparse map (k > 512)
+// The same recurrence on rows that hold only their finite entries, as ascending slot
+// lists (slots are numbered chain after chain, so slot order is chain order). One height
+// level per launch: every child of a node sits on a lower level, so a kernel boundary
+// separates a row from the rows it reads and there are no waits at all.
+
+// Ascending bitonic sort of p keys (p a power of two) by the calling warp, in global memory.
+__device__ void warp_bitonic_sort(unsigned long long *v, int64_t p) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t kk = 2; kk <= p; kk <<= 1) {
+        for (int64_t j = kk >> 1; j > 0; j >>= 1) {
+            for (int64_t i = lane; i < p; i += 32) {
+                const int64_t l = i ^ j;
+                if (l > i) {
+                    const unsigned long long x = v[i], y = v[l];
+                    if ((x > y) == ((i & kk) == 0)) {
+                        v[i] = y;
+                        v[l] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t row_of(const SparseLevelArgs &a, int32_t z) {
+    return (int64_t)a.node_slot[z] - a.chain_id[z] - 1;
+}
+
+// Candidate-list sizes of the level's nodes: the children's rows plus the own entry,
+// rounded up to a power of two for the sort. cand_off[1 + i] = size of node lo + i.
+__global__ void __launch_bounds__(kBuildThreads) k_sparse_bounds(SparseLevelArgs a) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = a.order[a.lo + i];
+        int64_t b = 1;
+        for (int64_t e = a.ptr[x]; e < a.ptr[x + 1]; ++e) b += a.row_len[row_of(a, a.adj[e])];
+        int64_t p = 1;
+        while (p < b) p <<= 1;
+        a.cand_off[1 + i] = p;
+        if (i == 0) a.cand_off[0] = 0;
+    }
+}
+
+// In-place inclusive scan of v[1 .. count] by one block (v[0] stays as it is).
+__global__ void __launch_bounds__(1024) k_scan_i64(int64_t *v, int64_t count) {
+    __shared__ int64_t s[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (count + 1023) / 1024;
+    const int64_t b = 1 + (int64_t)t * per, e = min(count + 1, b + per);
+    int64_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += v[i];
+    s[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t add = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += add;
+        __syncthreads();
+    }
+    int64_t run = t ? s[t - 1] : 0;
+    for (int64_t i = b; i < e; ++i) {
+        run += v[i];
+        v[i] = run;
+    }
+}
+
+// One warp per node of the level: gather the children's entries and the own one, sort
+// them by slot, keep the last (largest) slot of every chain's run, append the row to the
+// pool. The chain check, the U level and the row's length come out of the same passes.
+__global__ void __launch_bounds__(kBuildThreads) k_sparse_merge(SparseLevelArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (kBuildThreads / 32);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.cnt; i += nwarps) {
+        const int32_t x = a.order[a.lo + i];
+        const int32_t cx = a.chain_id[x], sx = a.node_slot[x];
+        const int64_t r = (int64_t)sx - cx - 1;
+        const int64_t off = a.cand_off[i], p = a.cand_off[i + 1] - off;
+        unsigned long long *v = a.cand + off;
+        int64_t L = 0;
+        int32_t m = a.base[cx];   // largest slot of x's own chain the children reach
+        for (int64_t e = a.ptr[x]; e < a.ptr[x + 1]; ++e) {
+            const int64_t rz = row_of(a, a.adj[e]);
+            const int64_t b = a.row_beg[rz];
+            const int32_t len = a.row_len[rz];
+            if (L + len + 1 > p) break;   // cannot happen: p covers every child's row
+            for (int32_t q = lane; q < len; q += 32) {
+                const int32_t s2 = a.pool[b + q];
+                v[L + q] = (unsigned long long)(uint32_t)s2;
+                if (a.slot_chain[s2] == cx) m = max(m, s2);
+            }
+            L += len;
+        }
+        if (lane == 0) v[L] = (unsigned long long)(uint32_t)sx;
+        ++L;
+        for (int64_t q = L + lane; q < p; q += 32) v[q] = ~0ull;
+        m = __reduce_max_sync(kFull, m);
+        if (lane == 0 && m != sx - 1) atomicMax(a.bad, a.topo_pos[x]);
+        __syncwarp();
+        warp_bitonic_sort(v, p);
+        // pass 1: count the kept entries, U level over the other chains
+        int32_t nk = 0, u = 0;
+        for (int64_t q0 = 0; q0 < L; q0 += 32) {
+            const int64_t q = q0 + lane;
+            bool keep = false;
+            if (q < L) {
+                const int32_t s2 = (int32_t)v[q];
+                const int32_t c = a.slot_chain[s2];
+                keep = q == L - 1 || a.slot_chain[(int32_t)v[q + 1]] != c;
+                if (keep && c != cx) u = max(u, a.uslot[s2] + 1);
+            }
+            nk += __popc(__ballot_sync(kFull, keep));
+        }
+        u = __reduce_max_sync(kFull, u);
+        unsigned long long beg = 0;
+        if (lane == 0) beg = atomicAdd(a.pool_top, (unsigned long long)nk);
+        beg = __shfl_sync(kFull, beg, 0);
+        if ((int64_t)(beg + nk) > a.pool_cap) {   // cannot happen: the host sized the pool
+            if (lane == 0) atomicCAS(a.status, 0u, (uint32_t)MZ_ERR_OOM);
+            continue;
+        }
+        // pass 2: write the kept entries in slot order
+        int32_t run = 0;
+        for (int64_t q0 = 0; q0 < L; q0 += 32) {
+            const int64_t q = q0 + lane;
+            bool keep = false;
+            int32_t s2 = 0;
+            if (q < L) {
+                s2 = (int32_t)v[q];
+                keep = q == L - 1 || a.slot_chain[(int32_t)v[q + 1]] != a.slot_chain[s2];
+            }
+            const unsigned mask = __ballot_sync(kFull, keep);
+            if (keep) a.pool[beg + run + __popc(mask & lt)] = s2;
+            run += __popc(mask);
+        }
+        if (lane == 0) {
+            a.row_beg[r] = (int64_t)beg;
+            a.row_len[r] = nk;
+            a.uslot[sx] = u;
+        }
+    }
+}
+
+// Sparse tiles: one warp per tile of 32 rows, lane = row; entries in slot order, then 0
+// (slot 0, a zero slot) up to the tile's row length.
+__global__ void __launch_bounds__(kBuildThreads) k_build_tiles_sparse(const int64_t *row_beg, const int32_t *row_len,
+                                                                     const int32_t *pool, int64_t n, int64_t ntiles,
+                                                                     const int64_t *tile_off, const int32_t *tile_k,
+                                                                     int32_t *Nt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (kBuildThreads / 32);
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nwarps) {
+        const int64_t r = t * 32 + lane;
+        const int64_t b = r < n ? row_beg[r] : 0;
+        const int32_t len = r < n ? row_len[r] : 0;
+        int32_t *dst = Nt + tile_off[t] + lane;
+        for (int32_t q = 0; q < tile_k[t]; ++q) dst[(int64_t)q * 32] = q < len ? pool[b + q] : 0;
+    }
+}
+
+// Moebius rows from sparse rows: one warp per row of the schedule; entries ranked by
+// (key of the element in the slot, slot), the other chains only. Keys go through
+// shared memory 256 at a time, so rows of any length work.
+constexpr int kRankTile = 256;
+__global__ void __launch_bounds__(kBuildThreads) k_build_mob_rows_sparse(BuildMobSparseArgs a) {
+    __shared__ unsigned long long s_key[kBuildThreads / 32][kRankTile];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (kBuildThreads / 32);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.n; i += nwarps) {
+        const int64_t r = a.mrow[i];
+        const int32_t sx = a.mslot[i];
+        const int64_t b = a.row_beg[r];
+        const int32_t len = a.row_len[r];
+        const int32_t cnt = len - 1;   // the own chain's entry is left out
+        if (cnt > a.mkp[i] || cnt < 0) continue;   // cannot happen for rows built by k_sparse_merge
+        int32_t *dst = a.Nm + a.moff[i] + a.mkp[i] - cnt;
+        for (int32_t q0 = 0; q0 < len; q0 += 32) {
+            const int32_t q = q0 + lane;
+            unsigned long long key = ~0ull;
+            int32_t s2 = sx;
+            if (q < len) {
+                s2 = a.pool[b + q];
+                if (s2 != sx) key = ((unsigned long long)(uint32_t)a.key_slot[s2] << 32) | (uint32_t)s2;
+            }
+            int32_t rank = 0;
+            for (int32_t t0 = 0; t0 < len; t0 += kRankTile) {
+                __syncwarp();
+                for (int32_t t = lane; t < kRankTile && t0 + t < len; t += 32) {
+                    const int32_t s3 = a.pool[b + t0 + t];
+                    s_key[w][t] = s3 == sx ? ~0ull : ((unsigned long long)(uint32_t)a.key_slot[s3] << 32) | (uint32_t)s3;
+                }
+                __syncwarp();
+                const int32_t tn = min(kRankTile, len - t0);
+                for (int32_t t = 0; t < tn; ++t) rank += s_key[w][t] < key;
+            }
+            if (key != ~0ull) dst[rank] = s2;
+        }
+    }
+}
+
 int kj_for(int32_t k) {
     int kj = 1;
     while (32 * kj < k) kj *= 2;
@@ -259,6 +460,38 @@ cudaError_t launch_build_tiles(const int32_t *N, int64_t n, int32_t k, int32_t *
     const int64_t ntiles = (n + 31) / 32;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms * 8));
     k_build_tiles<<<(unsigned)blocks, kBuildThreads, 0, st>>>(N, n, k, ntiles, Nt);
+    return cudaGetLastError();
+}
+
+static int64_t warp_blocks(int64_t items, int num_sms) {
+    return std::max<int64_t>(1, std::min<int64_t>((items + kBuildThreads / 32 - 1) / (kBuildThreads / 32),
+                                                  (int64_t)num_sms * 8));
+}
+
+cudaError_t launch_sparse_bounds(const SparseLevelArgs &a, int num_sms, cudaStream_t st) {
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((a.cnt + kBuildThreads - 1) / kBuildThreads,
+                                                                  (int64_t)num_sms * 8));
+    k_sparse_bounds<<<(unsigned)blocks, kBuildThreads, 0, st>>>(a);
+    if (cudaError_t e = cudaGetLastError()) return e;
+    k_scan_i64<<<1, 1024, 0, st>>>(a.cand_off, a.cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_merge(const SparseLevelArgs &a, int num_sms, cudaStream_t st) {
+    k_sparse_merge<<<(unsigned)warp_blocks(a.cnt, num_sms), kBuildThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_tiles_sparse(const int64_t *row_beg, const int32_t *row_len, const int32_t *pool, int64_t n,
+                                      int64_t ntiles, const int64_t *tile_off, const int32_t *tile_k, int32_t *Nt,
+                                      int num_sms, cudaStream_t st) {
+    k_build_tiles_sparse<<<(unsigned)warp_blocks(ntiles, num_sms), kBuildThreads, 0, st>>>(row_beg, row_len, pool, n,
+                                                                                            ntiles, tile_off, tile_k, Nt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_mob_rows_sparse(const BuildMobSparseArgs &a, int num_sms, cudaStream_t st) {
+    k_build_mob_rows_sparse<<<(unsigned)warp_blocks(a.n, num_sms), kBuildThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -212,14 +212,15 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const s
     }
 
     if (device_niv) {
-        // Steps 5 and the U levels of step 6 run on the device; the host keeps the
-        // children lists for the upload and computes the heights (one pass over the edges).
-        if (niv_format == 2 || k > kDenseMaxChains) {
-            err = "the device build keeps a dense niv map: it needs k <= " + std::to_string(kDenseMaxChains) +
-                  " chains (this poset has " + std::to_string(k) + ") and niv_format 0 or 1";
+        // Steps 5 and the U levels of step 6 run on the device (dense or sparse map, as
+        // below); the host keeps the children lists for the upload and computes the
+        // heights (one pass over the edges).
+        H.sparse = niv_format == 2 || (niv_format == 0 && k > kDenseMaxChains);
+        if (!H.sparse && k > kDenseMaxChains) {
+            err = "the device build keeps a dense niv map for k <= " + std::to_string(kDenseMaxChains) +
+                  " chains only (this poset has " + std::to_string(k) + "); use niv_format 0 or 2";
             return MZ_ERR_UNSUPPORTED;
         }
-        H.sparse = false;
         H.niv_on_device = true;
         H.level.assign(n, 1);
         for (int64_t i = n - 1; i >= 0; --i) {

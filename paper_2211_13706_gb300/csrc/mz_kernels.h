@@ -101,6 +101,48 @@ struct BuildMobArgs {
     int32_t *Nm;                // out, zeroed before the launch
 };
 
+// Sparse map, one height level [lo, lo + cnt) of `order` per launch pair.
+struct SparseLevelArgs {
+    const int64_t *ptr;
+    const int32_t *adj;
+    const int32_t *order;
+    int64_t lo, cnt;
+    const int32_t *node_slot;
+    const int32_t *chain_id;
+    const int32_t *slot_chain;  // [n + k] chain of each slot
+    const int32_t *base;        // [k] zero slot of each chain
+    const int32_t *topo_pos;
+    int64_t *row_beg;           // [n] out: start of row r in pool
+    int32_t *row_len;           // [n] out: its length (finite entries, own chain included)
+    int32_t *pool;              // rows, appended in any order
+    unsigned long long *pool_top;
+    int64_t pool_cap;           // entries the pool holds
+    int64_t *cand_off;          // [cnt + 1] candidate-list offsets (written by launch_sparse_bounds)
+    unsigned long long *cand;   // candidate lists (scratch)
+    int32_t *uslot;
+    int32_t *bad;
+    uint32_t *status;
+};
+
+struct BuildMobSparseArgs {
+    const int64_t *row_beg;
+    const int32_t *row_len;
+    const int32_t *pool;
+    const int32_t *mrow;
+    const int64_t *moff;
+    const int32_t *mkp;
+    const int32_t *mslot;
+    const int32_t *key_slot;
+    int64_t n;
+    int32_t *Nm;
+};
+
+cudaError_t launch_sparse_bounds(const SparseLevelArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_sparse_merge(const SparseLevelArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_build_tiles_sparse(const int64_t *row_beg, const int32_t *row_len, const int32_t *pool, int64_t n,
+                                      int64_t ntiles, const int64_t *tile_off, const int32_t *tile_k, int32_t *Nt,
+                                      int num_sms, cudaStream_t st);
+cudaError_t launch_build_mob_rows_sparse(const BuildMobSparseArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_build_niv(const BuildNivArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_build_tiles(const int32_t *N, int64_t n, int32_t k, int32_t *Nt, int num_sms, cudaStream_t st);
 cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream_t st);

@@ -24,13 +24,10 @@ def test_device_build_argument_checks():
     with pytest.raises(mz.MzError) as e:
         mz.mz_build_batch([(p.n, p.src, p.dst, None)] * 2, device_build=True)
     assert e.value.status == mz.MZ_ERR_UNSUPPORTED
-    # sparse niv maps stay on the host: refused before any device work
+    # a dense map on the device holds at most 512 chains: refused before any device work
+    q = pg.antichain_poset(600)
     with pytest.raises(mz.MzError) as e:
-        mz.mz_build(p.n, p.src, p.dst, device_build=True, niv_format=2)
-    assert e.value.status == mz.MZ_ERR_UNSUPPORTED
-    q = pg.antichain_poset(600)                     # 600 chains > 512
-    with pytest.raises(mz.MzError) as e:
-        mz.mz_build(q.n, q.src, q.dst, device_build=True)
+        mz.mz_build(q.n, q.src, q.dst, device_build=True, niv_format=1)
     assert e.value.status == mz.MZ_ERR_UNSUPPORTED and "512" in str(e.value)
 
 
@@ -125,3 +122,82 @@ def test_device_build_full_size_planted():
         assert host.info[key] == dev.info[key], key
     for w in (mz.MZ_EXPORT_NIV, mz.MZ_EXPORT_ULEVEL):
         assert np.array_equal(host.export(w), dev.export(w)), w
+
+
+def _sparse_cases():
+    pl7 = pg.planted_chain_poset(500, 7, 2, cross_p=5 / 500)
+    return [
+        ("paper_example", pg.paper_example(), None, 2),
+        ("planted_500_k7", pl7, pl7.chain_id, 2),
+        ("boolean_lattice_7", pg.boolean_lattice(7), None, 2),
+        ("antichain_600", pg.antichain_poset(600), None, 0),
+        ("er_3000_deg4", pg.er_dag(3000, 4, 11), None, 0),
+        ("er_2000_deg6", pg.er_dag(2000, 6, 12), None, 0),
+    ]
+
+
+SPARSE_CASES = _sparse_cases()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,p,cid,fmt", SPARSE_CASES, ids=[c[0] for c in SPARSE_CASES])
+@pytest.mark.parametrize("schedule", [mz.MZ_SCHED_ULEVEL, mz.MZ_SCHED_ANTICHAIN])
+def test_sparse_device_build_equals_host_build(name, p, cid, fmt, schedule):
+    host, dev = _pair(p, cid, build_transpose=True, mobius_schedule=schedule, niv_format=fmt)
+    assert dev.info["sparse"] == 1
+    for key in INFO_KEYS:
+        assert host.info[key] == dev.info[key], key
+    for dual in (False, True):
+        for w in EXPORTS:
+            assert np.array_equal(host.export(w, dual=dual), dev.export(w, dual=dual)), (w, dual)
+    Z = oracle.closure(p.n, p.src, p.dst)
+    chains = dev.export(mz.MZ_EXPORT_CHAIN_ID)
+    assert np.array_equal(dev.export(mz.MZ_EXPORT_NIV), oracle.niv(Z, chains))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,p,cid,fmt", SPARSE_CASES[3:], ids=[c[0] for c in SPARSE_CASES[3:]])
+def test_sparse_device_built_transforms_bit_identical(name, p, cid, fmt):
+    import torch
+    host, dev = _pair(p, cid, build_transpose=True, niv_format=fmt)
+    xi = torch.from_numpy(pg.function_values(p.n, 2, "i64:1000", 6)).cuda()
+    xf = torch.from_numpy(pg.function_values(p.n, 2, "f64u", 7)).cuda()
+    for op in ("zeta", "mobius", "zeta_T", "mobius_T"):
+        for x in (xi, xf):
+            a = getattr(host, op)(x)
+            b = getattr(dev, op)(x)
+            host.check()
+            dev.check()
+            assert torch.equal(a, b), op
+
+
+@pytest.mark.gpu
+def test_sparse_device_build_bad_chains_same_error():
+    p = pg.planted_chain_poset(2000, 8, 4, cross_deg=2)
+    bad = p.chain_id.copy()
+    bad[np.flatnonzero(bad == 0)[len(bad) // 40]] = 1
+    errs = []
+    for device_build in (False, True):
+        with pytest.raises(mz.MzError) as e:
+            mz.mz_build(p.n, p.src, p.dst, bad, device_build=device_build, niv_format=2)
+        errs.append((e.value.status, str(e.value).split(":", 1)[-1]))
+    assert errs[0][0] == errs[1][0] == mz.MZ_ERR_BAD_CHAINS
+    assert errs[0][1] == errs[1][1]
+
+
+@pytest.mark.gpu
+def test_sparse_device_build_er_paper_scale():
+    """The paper's ER DAG at n = 2^20, average degree 4 (path cover, k ~ 0.27 n): plan info, U
+    levels and the fp64 transforms equal the host-built plan's bit for bit."""
+    import torch
+    p = pg.er_dag(1 << 20, 4, 1)
+    host, dev = _pair(p, None)
+    for key in INFO_KEYS:
+        assert host.info[key] == dev.info[key], key
+    assert np.array_equal(host.export(mz.MZ_EXPORT_ULEVEL), dev.export(mz.MZ_EXPORT_ULEVEL))
+    x = torch.from_numpy(pg.function_values(p.n, 1, "f64u", 8)[:, 0]).cuda()
+    for op in ("zeta", "mobius"):
+        a, b = getattr(host, op)(x), getattr(dev, op)(x)
+        host.check()
+        dev.check()
+        assert torch.equal(a, b), op
