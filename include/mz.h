@@ -91,7 +91,7 @@ typedef struct {
     int32_t mobius_pace_ns;   /* Moebius forward substitution: before polling for a row that is
                                  d levels above the row it just finished, a thread sleeps about
                                  (d - 2) * pace ns, so rows far from the frontier do not load L2
-                                 with polls. 0 = default (1000); negative = no pacing */
+                                 with polls. 0 = default (500); negative = no pacing */
     int32_t niv_format;       /* 0: dense niv map (k entries per node) unless k > 512, then sparse
                                  (only the finite entries, nnz(N) of Sec. 2.4); 1: dense; 2: sparse */
     int64_t spin_limit;       /* bound on polling iterations of every device-side wait; 0 = default (2^22) */

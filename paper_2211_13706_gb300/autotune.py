@@ -16,7 +16,7 @@ from . import mz_plan_tune
 
 CANDIDATES = {
     "mobius_blocks_per_sm": (1, 2, 3, 4),
-    "mobius_pace_ns": (500, 1000, 2000),
+    "mobius_pace_ns": (300, 500, 800, 1500),
     "gather_blocks_per_sm": (8, 16, 32),
 }
 _CACHE: dict = {}

@@ -108,7 +108,7 @@ struct mz_plan {
     int device = -1;
     int num_sms = 0;
     int32_t mob_blocks_per_sm = 2;  // one-thread-per-row wavefront: blocks of 128 threads per SM
-    int32_t mob_pace_ns = 1000;     // wavefront pacing per level of distance (0: none)
+    int32_t mob_pace_ns = 500;      // wavefront pacing per level of distance (0: none)
     int32_t gather_blocks_per_sm = 32;
     int64_t device_bytes = 0;
     std::vector<void *> allocations;

@@ -329,7 +329,7 @@ __device__ __forceinline__ T shfl_xor_t(T v, int off) {
 // Sums the NV words v[j] = P[id[j]] into acc (or subtracts them, SUB) in column order, adding each one as
 // soon as it and all before it are present: columns are sorted by dependency
 // level, so words land roughly in order and when the last one lands only one
-// addition is left. The first missing word is polled with two loads in flight;
+// addition is left. The first missing word is polled, one request per round;
 // once it lands every later missing word is requested again in one round.
 template <class M, int NV, bool SUB>
 __device__ __forceinline__ void sum_in_order(unsigned long long *v, const int32_t *id, const unsigned long long *P,
@@ -350,10 +350,8 @@ __device__ __forceinline__ void sum_in_order(unsigned long long *v, const int32_
 #pragma unroll
         for (int j = 0; j < NV; ++j)
             if (j == next) addr = P + id[j];
-        const unsigned long long a0 = ld_relaxed_u64(addr);
-        __nanosleep(32);
-        const unsigned long long a1 = ld_relaxed_u64(addr);
-        const unsigned long long got = a0 != S ? a0 : a1;
+        // no pause between rounds: a sleep, however short, costs a round trip per level
+        const unsigned long long got = ld_relaxed_u64(addr);
         if (got != S) {
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
