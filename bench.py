@@ -271,38 +271,55 @@ def time_transforms(mz, plan, x, steps, warmup, torch, flush, anti=False, sample
 
 
 def time_e2e(mz, plan, f_np, dtype_key, steps, torch):
-    """Same step through the public API from pinned host memory: H2D of f, zeta,
-    Moebius, D2H of both results, all inside the timed events. The zeta result goes
-    back to the host on a second stream while the Moebius transform runs."""
+    """The step through the public API from pinned host memory: H2D of f, zeta, Moebius,
+    D2H of both results, every step inside the timed region. Double-buffered on three
+    streams: step i+1's input goes up and step i's results come down while the GPU
+    computes, as a user streaming many functions through one plan would run it."""
     x = to_dev(f_np, dtype_key, torch)
     h_in = x.cpu().pin_memory()
-    h_g = torch.empty_like(h_in).pin_memory()
-    h_f = torch.empty_like(h_in).pin_memory()
-    d_in = torch.empty_like(x)
-    d_g = torch.empty_like(x)
-    d_f = torch.empty_like(x)
-    st = torch.cuda.current_stream()
-    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    d_in = [torch.empty_like(x) for _ in range(2)]
+    d_g = [torch.empty_like(x) for _ in range(2)]
+    d_f = [torch.empty_like(x) for _ in range(2)]
+    h_g = [torch.empty_like(h_in).pin_memory() for _ in range(2)]
+    h_f = [torch.empty_like(h_in).pin_memory() for _ in range(2)]
+    ev = lambda: [torch.cuda.Event() for _ in range(2)]
+    uploaded, g_ready, f_ready, downloaded = ev(), ev(), ev(), ev()
+
+    def run(nsteps):
+        for i in range(nsteps):
+            s = i % 2
+            if i >= 2:
+                up.wait_event(g_ready[s])          # step i-2 has read d_in[s]
+            with torch.cuda.stream(up):
+                d_in[s].copy_(h_in, non_blocking=True)
+            uploaded[s].record(up)
+            main.wait_event(uploaded[s])
+            if i >= 2:
+                main.wait_event(downloaded[s])     # step i-2's results are on the host
+            plan.zeta(d_in[s], out=d_g[s])
+            g_ready[s].record(main)
+            plan.mobius(d_g[s], out=d_f[s])
+            f_ready[s].record(main)
+            down.wait_event(g_ready[s])
+            with torch.cuda.stream(down):
+                h_g[s].copy_(d_g[s], non_blocking=True)
+            down.wait_event(f_ready[s])
+            with torch.cuda.stream(down):
+                h_f[s].copy_(d_f[s], non_blocking=True)
+            downloaded[s].record(down)
+        main.wait_stream(down)
+
+    run(2)                                          # warm-up
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g_ready, g_copied = torch.cuda.Event(), torch.cuda.Event()
-    total = 0.0
-    for it in range(steps + 2):
-        torch.cuda.synchronize()
-        e0.record(st)
-        d_in.copy_(h_in, non_blocking=True)
-        plan.zeta(d_in, out=d_g)
-        g_ready.record(st)
-        side.wait_event(g_ready)
-        with torch.cuda.stream(side):
-            h_g.copy_(d_g, non_blocking=True)
-        g_copied.record(side)
-        plan.mobius(d_g, out=d_f)
-        h_f.copy_(d_f, non_blocking=True)
-        st.wait_event(g_copied)
-        e1.record(st)
-        e1.synchronize()
-        if it >= 2:
-            total += e0.elapsed_time(e1)
+    e0.record(main)
+    up.wait_stream(main)
+    run(steps)
+    e1.record(main)
+    e1.synchronize()
+    total = e0.elapsed_time(e1)
     plan.check()
     nbytes = x.numel() * x.element_size()
     return total, nbytes, 2 * nbytes
@@ -416,6 +433,69 @@ def run_batch_workload(mz, wl, posets, steps, warmup, torch, dtypes=("f32c", "f6
         del x
         torch.cuda.empty_cache()
     plan.close()
+    return out
+
+
+def time_seeds(mz, torch, wl: str, dtype_key: str, flush, seeds=(1, 2, 3, 4, 5), steps: int = 20):
+    """The headline step (zeta + Moebius, B = 1) on the workload drawn with each seed; plans
+    built on the device. Returns per-seed node-values/s and their median."""
+    vals = []
+    for sd in seeds:
+        p = make_poset(wl, sd)
+        plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, device_build=True)
+        x = to_dev(pg.function_values(p.n, 1, DTYPES[dtype_key][0], 2)[:, 0], dtype_key, torch)
+        g, y = plan.zeta(x), None
+        y = plan.mobius(g)
+        ts = []
+        for it in range(steps + 3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.zeta(x, out=g)
+            plan.mobius(g, out=y)
+            e1.record()
+            e1.synchronize()
+            if it >= 3:
+                ts.append(e0.elapsed_time(e1))
+        plan.check()
+        vals.append(round(2 * p.n / (statistics.median(ts) / 1e3), 1))
+        plan.close()
+    return {"seeds": list(seeds), "values": vals, "median": statistics.median(vals), "unit": UNIT,
+            "note": "median step time of 20 per seed, L2 flushed between steps"}
+
+
+def cpu_paper_method(mz, plan, f_np, dtype_key, gpu_g=None):
+    """The paper's fast transforms on the host cores (cpubase/: Alg. 3, Alg. 4 in Alg. 5's
+    antichain order, OpenMP), timed on this plan's structures: all threads and one."""
+    import cpubase
+    if plan.info["sparse"]:
+        return None
+    cp = cpubase.CpuPlan(plan, mz.MZ_EXPORT_NIV, mz.MZ_EXPORT_CHAIN_ID, mz.MZ_EXPORT_CHAIN_POS, mz.MZ_EXPORT_LEVEL)
+    x = np.asarray(f_np, np.int64 if dtype_key == "i64" else np.float64)
+    out = {"kind": "paper_method_cpu", "dtype": "int64" if dtype_key == "i64" else "f64"}
+    all_threads = cpubase.threads()
+    for label, t, reps in (("all_cores", all_threads, 3), ("one_core", 1, 1)):
+        cpubase.set_threads(t)
+        tz, tm = [], []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            g = cp.zeta(x)
+            t1 = time.perf_counter()
+            y = cp.mobius(g)
+            t2 = time.perf_counter()
+            tz.append(t1 - t0)
+            tm.append(t2 - t1)
+        z, m = statistics.median(tz), statistics.median(tm)
+        out[label] = {"threads": t, "zeta_ms": round(z * 1e3, 2), "mobius_ms": round(m * 1e3, 2),
+                      "value": round(2 * plan.info["n"] / (z + m), 1), "unit": UNIT}
+    cpubase.set_threads(all_threads)
+    if dtype_key == "i64":   # exact: Moebius(zeta(f)) = f
+        out["check"] = {"moebius_of_zeta_is_f": bool(np.array_equal(y, x))}
+    elif gpu_g is not None:  # fp64 Moebius at this size is too ill-conditioned for a round trip
+        err = float(np.max(np.abs(g - gpu_g)) / max(1e-300, float(np.max(np.abs(gpu_g)))))
+        out["check"] = {"zeta_vs_gpu_max_rel": err}
+    out["note"] = ("transforms only, on the plan's chains, dense niv map and antichain levels; "
+                   "the fair CPU reference point for the GPU numbers")
     return out
 
 
@@ -575,6 +655,7 @@ def device_arm(args):
         pa = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
         kta, tot, _, _, _, _ = time_transforms(mz, pa, x, 3, 1, torch, flush, anti=True)
         variants["differentiation_c5"] = time_differentiation(mz, torch)
+        variants["seeds_1_to_5"] = time_seeds(mz, torch, args.workload, args.dtype, flush)
         variants["paper_er_n2^20_deg4"] = time_single(mz, torch, "er1m4", args.dtype)
         variants["paper_er_n2^20_deg6"] = time_single(mz, torch, "er1m6", args.dtype)
         if batch_posets is not None:
@@ -585,9 +666,11 @@ def device_arm(args):
             "note": "Alg. 5/6 schedule (antichain levels) instead of U's dependency levels"}
         pa.close()
 
-    cpu = None
+    cpu = cpu_fast = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(p, f_np, args.cpu_budget, 64)
+        if args.dtype in ("f64", "i64"):
+            cpu_fast = cpu_paper_method(mz, plan, f_np, args.dtype, g.cpu().numpy())
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -603,8 +686,10 @@ def device_arm(args):
         "latency_roof": latency,
         "kernels": kernels,
         "cpu_baseline": cpu,
+        "cpu_paper_method": cpu_fast,
         "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": round(e2e_ms / e2e_steps, 5)},
+                "ms_per_step": round(e2e_ms / e2e_steps, 5),
+                "copies": "pinned host memory; double-buffered: step i+1's H2D and step i's D2H overlap compute"},
         "gpu_launches": launches,
         "clocks": clocks,
         "variants": variants,
