@@ -423,13 +423,38 @@ def run_batch_workload(mz, wl, posets, steps, warmup, torch, dtypes=("f32c", "f6
     info = plan.info
     out = {"workload": w["desc"], "posets": info["components"], "n_total": info["n"], "k_total": info["k"],
            "nnz": info["nnz"], "max_ulevels": info["ulevels"], "batch": w["batch"], "host_build_s": round(build_s, 1)}
+    peak, peak_kind = load_peaks()
+    n, k, B, nnz = info["n"], info["k"], w["batch"], info["nnz"]
     for dk in dtypes:
-        x = batch_values(info["n"], w["batch"], dk, 11, torch)
+        x = batch_values(n, B, dk, 11, torch)
         tuned = autotune.tune(plan, x)
         tot, used_graph = time_batch(mz, plan, x, steps, warmup, torch, graph)
-        units = 2 * info["n"] * w["batch"] * steps
+        units = 2 * n * B * steps
         out[dk] = {"value": round(units / (tot / 1e3), 1), "unit": UNIT, "ms_per_step": round(tot / steps, 3),
                    "steps": steps, "cuda_graph": used_graph, "tuning": tuned}
+        # per-kernel times of the same step, launched directly (inputs exceed L2: no flush)
+        kt, _, _, _, _, _ = time_transforms(mz, plan, x, 3, 1, torch, torch.empty(1, device="cuda"))
+        out[dk]["kernels"] = {name: {"mean_ms": round(v, 4), "share": round(v / sum(kt.values()), 4),
+                                     "alg_GBps": round(algorithmic_bytes(name, n, k, B, nnz) / (v / 1e3) / 1e9, 1)}
+                              for name, v in kt.items()}
+        dom = max(kt, key=kt.get)
+        alg = algorithmic_bytes(dom, n, k, B, nnz)
+        achieved = alg / (kt[dom] / 1e3) / 1e9
+        out[dk]["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                               "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                               "traffic": None, "algorithmic_bytes": alg}
+        # the gather's arithmetic roof: one add per gathered term and function
+        terms = nnz * B
+        t_g = kt["niv_gather"] / 1e3
+        if dk == "f32c":     # Sum2 step: TwoSum (6 fp32 adds) + 2 adds per term
+            ops, peak_ops = 8 * terms, torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2.07e9
+            out[dk]["gather_alu"] = {"fp32_ops": ops, "achieved_Tops": round(ops / t_g / 1e12, 2),
+                                     "peak_Tops": round(peak_ops / 1e12, 2), "frac": round(ops / t_g / peak_ops, 4),
+                                     "note": "peak = SMs x 128 fp32 lanes x 2.07 GHz (one add per lane per clock)"}
+        elif dk == "f64":
+            out[dk]["gather_alu"] = {"fp64_adds": terms, "achieved_Tadds": round(terms / t_g / 1e12, 3),
+                                     "peak_Tadds": FP64_ADDS_PER_S / 1e12,
+                                     "frac": round(terms / t_g / FP64_ADDS_PER_S, 4)}
         del x
         torch.cuda.empty_cache()
     plan.close()
@@ -732,6 +757,7 @@ def batch_arm(args, posets):
                        "units": "2*n*B node-values per step", "host_build_s": res["host_build_s"],
                        "cuda_graph": main["cuda_graph"], "tuning": main["tuning"],
                        "parallelism": f"replicas x{world}"},
+            "roofline": main["roofline"], "kernels": main["kernels"], "gather_alu": main.get("gather_alu"),
             "fp64_plain": res.get("f64"), "clocks": clocks, "gpu_launches": 5 * main["steps"]}
     print(json.dumps(line))
 

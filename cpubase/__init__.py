@@ -43,7 +43,7 @@ def _load():
         lib.mzcpu_threads.restype = ctypes.c_int
         lib.mzcpu_set_threads.argtypes = [ctypes.c_int]
         for suf in ("f64", "i64"):
-            getattr(lib, f"mzcpu_zeta_{suf}").argtypes = [i64, i32, i64, vp, vp, vp, vp, vp]
+            getattr(lib, f"mzcpu_zeta_{suf}").argtypes = [i64, i32, vp, vp, vp, vp, vp, vp]
             getattr(lib, f"mzcpu_mobius_{suf}").argtypes = [i64, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         _lib = lib
     return _lib
@@ -71,6 +71,7 @@ class CpuPlan:
         lens = np.bincount(chain, minlength=k)
         base = np.concatenate([[0], np.cumsum(lens + 1)])[:k]
         self.S = int(n + k)
+        self.chain_base = np.ascontiguousarray(np.concatenate([base, [self.S]]).astype(np.int64))
         self.node_slot = np.ascontiguousarray((base[chain] + 1 + pos).astype(np.int32))
         self.slot_node = np.full(self.S, -1, np.int32)
         self.slot_node[self.node_slot] = np.arange(n, dtype=np.int32)
@@ -96,8 +97,8 @@ class CpuPlan:
         f, suf, dt = self._prep(f)
         g = np.empty(self.n, dt)
         P = np.empty(self.S, dt)
-        getattr(_load(), f"mzcpu_zeta_{suf}")(self.n, self.k, self.S, self._ptr(self.slot_node), self._ptr(self.N),
-                                               self._ptr(f), self._ptr(g), self._ptr(P))
+        getattr(_load(), f"mzcpu_zeta_{suf}")(self.n, self.k, self._ptr(self.chain_base), self._ptr(self.slot_node),
+                                               self._ptr(self.N), self._ptr(f), self._ptr(g), self._ptr(P))
         return g
 
     def mobius(self, g):

@@ -8,6 +8,7 @@
  * (0 = bottom) sits at slot base_c + 1 + p.
  *   node_slot[n]     slot of each node
  *   slot_node[S]     node of each slot, -1 at the zero slots (S = n + k)
+ *   chain_base[k+1]  first slot (the zero slot) of each chain, chain_base[k] = S
  *   N[n * k]         N[x * k + c] = slot of niv_c(x), or base_c when there is none
  *   chain_of[n]      chain of each node
  *   lvl_ptr[L + 1], lvl_nodes[n]   antichain levels from the bottom (heights)
@@ -43,15 +44,15 @@ void mzcpu_set_threads(int t) {
 }
 
 #define MZCPU_DEFINE(T, SUF)                                                                            \
-    void mzcpu_zeta_##SUF(int64_t n, int32_t k, int64_t S, const int32_t *slot_node, const int32_t *N,   \
-                          const T *f, T *g, T *P) {                                                     \
-        int64_t s, x;                                                                                   \
-        /* one task per chain: a zero slot starts it, the running sum fills its slots */               \
-        _Pragma("omp parallel for schedule(dynamic, 1)") for (s = 0; s < S; ++s) {                     \
-            if (slot_node[s] >= 0) continue;                                                            \
+    void mzcpu_zeta_##SUF(int64_t n, int32_t k, const int64_t *chain_base, const int32_t *slot_node,     \
+                          const int32_t *N, const T *f, T *g, T *P) {                                   \
+        int64_t x;                                                                                      \
+        int32_t c;                                                                                      \
+        /* one task per chain: its zero slot, then the running sum over its slots */                   \
+        _Pragma("omp parallel for schedule(dynamic, 1)") for (c = 0; c < k; ++c) {                     \
             T run = 0;                                                                                  \
-            P[s] = 0;                                                                                   \
-            for (int64_t q = s + 1; q < S && slot_node[q] >= 0; ++q) {                                  \
+            P[chain_base[c]] = 0;                                                                       \
+            for (int64_t q = chain_base[c] + 1; q < chain_base[c + 1]; ++q) {                           \
                 run += f[slot_node[q]];                                                                 \
                 P[q] = run;                                                                             \
             }                                                                                           \
