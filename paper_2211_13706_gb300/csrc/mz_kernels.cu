@@ -276,8 +276,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
 }
 
 // Batched gather (B > 1, B a power of two): one warp per tile of 32 rows, G = min(B, 32)
-// lanes per row (lane b0 owns the columns b0 + G t), 32 / G rows at a time. Within a row
-// group the map entry is a broadcast and the G loads of y' are contiguous.
+// lanes per row (lane b0 owns the columns b0 + G t), 32 / G row pairs at a time (rows r and
+// r + 16: two independent sums, twice the loads in flight). Within a row group the map
+// entry is a broadcast and the G loads of y' are contiguous.
 template <class Pol, int G>
 __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a) {
     using P_t = typename Pol::P_t;
@@ -292,21 +293,38 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a
     for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
         const int k = a.tile_k[tile];
         const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
-        for (int r = sub; r < kTileRows; r += R) {
+        for (int r = sub; r < kTileRows / 2; r += R) {
+            const int r2 = r + kTileRows / 2;
             const int32_t node = a.row_node[tile * kTileRows + r];
-            if (node < 0) continue;
+            const int32_t node2 = a.row_node[tile * kTileRows + r2];
             for (int64_t b = b0; b < B; b += G) {
-                Acc acc = Pol::acc_zero();
+                Acc acc = Pol::acc_zero(), acc2 = Pol::acc_zero();
                 int c = 0;
                 for (; c + 8 <= k; c += 8) {
-                    int32_t sl[8];
+                    int32_t sl[8], sl2[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) sl[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r);
+                    for (int u = 0; u < 8; ++u) {
+                        sl[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r);
+                        sl2[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r2);
+                    }
+                    P_t v[8], v2[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) Pol::acc_add(acc, __ldg(P + (int64_t)sl[u] * B + b));
+                    for (int u = 0; u < 8; ++u) {
+                        v[u] = __ldg(P + (int64_t)sl[u] * B + b);
+                        v2[u] = __ldg(P + (int64_t)sl2[u] * B + b);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        Pol::acc_add(acc, v[u]);
+                        Pol::acc_add(acc2, v2[u]);
+                    }
                 }
-                for (; c < k; ++c) Pol::acc_add(acc, __ldg(P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + r) * B + b));
-                Pol::store_out(a.g, (int64_t)node * B + b, a.nB, acc);
+                for (; c < k; ++c) {
+                    Pol::acc_add(acc, __ldg(P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + r) * B + b));
+                    Pol::acc_add(acc2, __ldg(P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + r2) * B + b));
+                }
+                if (node >= 0) Pol::store_out(a.g, (int64_t)node * B + b, a.nB, acc);
+                if (node2 >= 0) Pol::store_out(a.g, (int64_t)node2 * B + b, a.nB, acc2);
             }
         }
     }
