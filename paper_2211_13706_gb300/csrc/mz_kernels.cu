@@ -7,8 +7,10 @@
 //                  scan with decoupled look-back", 2016).
 //   k_niv_gather   g(x) = sum_j c[niv_j(x)], Eq. (zeta-fast) = U c. One warp per
 //                  tile of 32 consecutive rows (one row per lane), the tiled map
-//                  streamed with coalesced loads; along a chain niv_j is monotone,
-//                  so a warp's 32 gathers of one column hit a narrow window of c.
+//                  streamed with coalesced loads, each group of 8 entries requested
+//                  while the previous group's values are gathered; along a chain
+//                  niv_j is monotone, so a warp's 32 gathers of one column hit a
+//                  narrow window of c.
 //   k_mob_init     fills y' with the "not ready" sentinel (0 at zero slots).
 //   k_mob_wave     forward substitution of Alg. 4, U y' = g:
 //                  y'(x) = g(x) - sum_{j != id(x)} y'(niv_j(x)),
@@ -250,15 +252,24 @@ __global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
 #pragma unroll
         for (int u = 0; u < BT; ++u) acc[u] = Pol::acc_zero();
         int c = 0;
-        for (; c + 8 <= k; c += 8) {
-            int32_t s[8];
+        int32_t s[8];
+        if (k >= 8) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) s[u] = __ldcs(np + (int64_t)(c + u) * kTileRows);
+            for (int u = 0; u < 8; ++u) s[u] = __ldcs(np + (int64_t)u * kTileRows);
+        }
+        for (; c + 8 <= k; c += 8) {
+            // the next 8 map entries are requested before this group's values are gathered
+            int32_t sn[8];
+            const bool more = c + 16 <= k;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sn[u] = more ? __ldcs(np + (int64_t)(c + 8 + u) * kTileRows) : 0;
 #pragma unroll
             for (int u = 0; u < 8; ++u)
 #pragma unroll
                 for (int q = 0; q < BT; ++q)
                     if (BT == 1 || b0 + q < a.B) Pol::acc_add(acc[q], __ldg(P + (int64_t)s[u] * a.B + b0 + q));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s[u] = sn[u];
         }
         for (; c < k; ++c) {
             const int32_t s = __ldcs(np + (int64_t)c * kTileRows);
