@@ -54,6 +54,41 @@ class _Opts(ctypes.Structure):
                 ("device_build", ctypes.c_int32)]
 
 
+# Plan memory through PyTorch's caching allocator (mz_build_opts::dev_alloc / dev_free):
+# the plan's buffers then show up in torch.cuda.memory_allocated and share its pool.
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def _torch_alloc(nbytes, ctx):
+    try:
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes))
+    except Exception:       # NULL: the library reports MZ_ERR_OOM
+        return None
+
+
+def _torch_free(ptr, ctx):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(ptr)
+    except Exception:       # interpreter shutdown: the process releases the memory
+        pass
+
+
+_TORCH_ALLOC = _ALLOC_T(_torch_alloc)
+_TORCH_FREE = _FREE_T(_torch_free)
+
+
+def _opts(build_transpose, host_only, mobius_schedule, mobius_blocks_per_sm, mobius_pace_ns, niv_format,
+          spin_limit, debug_withhold, device_build, torch_allocator):
+    alloc = ctypes.cast(_TORCH_ALLOC, ctypes.c_void_p).value if torch_allocator else None
+    free = ctypes.cast(_TORCH_FREE, ctypes.c_void_p).value if torch_allocator else None
+    return _Opts(int(build_transpose), int(host_only), int(mobius_schedule), int(mobius_blocks_per_sm),
+                 int(mobius_pace_ns), int(niv_format), int(spin_limit), int(debug_withhold), alloc, free, None,
+                 int(device_build))
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("mobius_blocks_per_sm", ctypes.c_int32), ("mobius_pace_ns", ctypes.c_int32),
                 ("gather_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -122,14 +157,15 @@ def _check(st: int, where: str):
 def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, host_only: bool = False,
              mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0,
              mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0, niv_format: int = 0,
-             device_build: bool = False) -> int:
-    """mz_build: returns the plan handle (an integer). Host arrays are int32."""
+             device_build: bool = False, torch_allocator: bool = False) -> int:
+    """mz_build: returns the plan handle (an integer). Host arrays are int32.
+    torch_allocator: the plan's device memory (and the build's scratch) comes from
+    PyTorch's caching allocator through the dev_alloc / dev_free callbacks."""
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
     cid = None if chain_id is None else np.ascontiguousarray(chain_id, dtype=np.int32)
-    opts = _Opts(int(build_transpose), int(host_only), int(mobius_schedule), int(mobius_blocks_per_sm),
-                 int(mobius_pace_ns), int(niv_format), int(spin_limit), int(debug_withhold), None, None, None,
-                 int(device_build))
+    opts = _opts(build_transpose, host_only, mobius_schedule, mobius_blocks_per_sm, mobius_pace_ns, niv_format,
+                 spin_limit, debug_withhold, device_build, torch_allocator)
     out = ctypes.c_void_p()
     st = lib.mz_build(int(n), int(src.size), src.ctypes.data, dst.ctypes.data,
                       None if cid is None else cid.ctypes.data, ctypes.byref(opts), ctypes.byref(out))
@@ -140,7 +176,7 @@ def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, 
 def mz_build_batch(posets, *, build_transpose: bool = False, host_only: bool = False,
                    mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0,
                    mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0, niv_format: int = 0,
-                   device_build: bool = False) -> int:
+                   device_build: bool = False, torch_allocator: bool = False) -> int:
     """mz_build_batch: `posets` is a list of (n, src, dst, chain_id or None)."""
     count = len(posets)
     ns = np.array([int(p[0]) for p in posets], dtype=np.int64)
@@ -150,9 +186,8 @@ def mz_build_batch(posets, *, build_transpose: bool = False, host_only: bool = F
     ms = np.array([a.size for a in srcs], dtype=np.int64)
     ptr = lambda arrs: (ctypes.c_void_p * count)(*[None if a is None else a.ctypes.data for a in arrs])
     psrc, pdst, pcid = ptr(srcs), ptr(dsts), ptr(cids)
-    opts = _Opts(int(build_transpose), int(host_only), int(mobius_schedule), int(mobius_blocks_per_sm),
-                 int(mobius_pace_ns), int(niv_format), int(spin_limit), int(debug_withhold), None, None, None,
-                 int(device_build))
+    opts = _opts(build_transpose, host_only, mobius_schedule, mobius_blocks_per_sm, mobius_pace_ns, niv_format,
+                 spin_limit, debug_withhold, device_build, torch_allocator)
     out = ctypes.c_void_p()
     st = lib.mz_build_batch(count, ns.ctypes.data, ms.ctypes.data, psrc, pdst,
                             None if all(c is None for c in cids) else pcid, ctypes.byref(opts), ctypes.byref(out))
@@ -278,6 +313,7 @@ class Plan:
         if getattr(self, "handle", None):
             mz_destroy(self.handle)
             self.handle = None
+        self._ws = {}
 
     def __del__(self):
         try:

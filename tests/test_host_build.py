@@ -170,3 +170,12 @@ def test_singletons_and_antichain():
     q = pg.antichain_poset(50)
     plan = mz.Plan(q.n, q.src, q.dst, None, host_only=True)
     assert plan.info["k"] == 50 and plan.info["nnz"] == 50 and plan.info["ulevels"] == 1
+
+
+def test_torch_allocator_option_on_host_only_plan():
+    # host-only plans allocate no device memory: the callbacks are set but never called
+    p = pg.paper_example()
+    plan = mz.Plan(p.n, p.src, p.dst, None, host_only=True, torch_allocator=True, build_transpose=True)
+    assert plan.info["device_bytes"] == 0
+    assert plan.export(mz.MZ_EXPORT_LEVEL).max() == 5
+    plan.close()
