@@ -708,6 +708,7 @@ static mz_status run_zeta(const mz_plan *p, int side, mz_dtype dtype, const void
     ga.P = w + L.P;
     ga.g = g;
     ga.nB = D.n * (int64_t)B;
+    ga.nslots = D.nslots;
     if ((e = launch_gather(dtype, ga, p->num_sms, s)) != cudaSuccess) return cuda_fail(e, "niv gather launch");
     mark_event(++g_last_launches, s);
     return MZ_OK;

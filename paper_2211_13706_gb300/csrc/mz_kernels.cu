@@ -289,8 +289,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
 // Batched gather (B > 1, B a power of two): one warp per tile of 32 rows, G = min(B, 32)
 // lanes per row (lane b0 owns the columns b0 + G t), 32 / G row pairs at a time (rows r and
 // r + 16: two independent sums, twice the loads in flight). Within a row group the map
-// entry is a broadcast and the G loads of y' are contiguous.
-template <class Pol, int G>
+// entry is a broadcast and the G loads of y' are contiguous. NARROW (nslots * B < 2^32):
+// y' offsets in 32-bit arithmetic, one instruction per address instead of a 64-bit multiply.
+template <class Pol, int G, bool NARROW>
 __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a) {
     using P_t = typename Pol::P_t;
     using Acc = typename Pol::Acc;
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const P_t *__restrict__ P = reinterpret_cast<const P_t *>(a.P);
     const int64_t B = a.B;
+    const uint32_t Bu = (uint32_t)a.B;
     for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
         const int k = a.tile_k[tile];
         const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
@@ -309,6 +311,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a
             const int32_t node = a.row_node[tile * kTileRows + r];
             const int32_t node2 = a.row_node[tile * kTileRows + r2];
             for (int64_t b = b0; b < B; b += G) {
+                const P_t *__restrict__ Pb = P + b;
                 Acc acc = Pol::acc_zero(), acc2 = Pol::acc_zero();
                 int c = 0;
                 for (; c + 8 <= k; c += 8) {
@@ -321,8 +324,13 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a
                     P_t v[8], v2[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        v[u] = __ldg(P + (int64_t)sl[u] * B + b);
-                        v2[u] = __ldg(P + (int64_t)sl2[u] * B + b);
+                        if (NARROW) {
+                            v[u] = __ldg(Pb + (uint32_t)sl[u] * Bu);
+                            v2[u] = __ldg(Pb + (uint32_t)sl2[u] * Bu);
+                        } else {
+                            v[u] = __ldg(Pb + (int64_t)sl[u] * B);
+                            v2[u] = __ldg(Pb + (int64_t)sl2[u] * B);
+                        }
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -650,13 +658,18 @@ static cudaError_t launch_gather_t(const GatherArgs &a, int num_sms, cudaStream_
     } else if ((a.B & (a.B - 1)) == 0) {
         const int G = a.B < 32 ? a.B : 32;
         const dim3 grid((unsigned)blocks, 1);
+        const bool narrow = a.nslots * (int64_t)a.B <= (int64_t)0xffffffffll;
+#define MZ_GATHER_B(g)                                                                   \
+    (narrow ? k_niv_gather_b<Pol, g, true><<<grid, kGatherThreads, 0, st>>>(a)             \
+            : k_niv_gather_b<Pol, g, false><<<grid, kGatherThreads, 0, st>>>(a))
         switch (G) {
-            case 2: k_niv_gather_b<Pol, 2><<<grid, kGatherThreads, 0, st>>>(a); break;
-            case 4: k_niv_gather_b<Pol, 4><<<grid, kGatherThreads, 0, st>>>(a); break;
-            case 8: k_niv_gather_b<Pol, 8><<<grid, kGatherThreads, 0, st>>>(a); break;
-            case 16: k_niv_gather_b<Pol, 16><<<grid, kGatherThreads, 0, st>>>(a); break;
-            default: k_niv_gather_b<Pol, 32><<<grid, kGatherThreads, 0, st>>>(a); break;
+            case 2: MZ_GATHER_B(2); break;
+            case 4: MZ_GATHER_B(4); break;
+            case 8: MZ_GATHER_B(8); break;
+            case 16: MZ_GATHER_B(16); break;
+            default: MZ_GATHER_B(32); break;
         }
+#undef MZ_GATHER_B
     } else {
         const unsigned gy = (unsigned)((a.B + 3) / 4);
         k_niv_gather<Pol, 4><<<dim3((unsigned)blocks, gy), kGatherThreads, 0, st>>>(a);

@@ -44,6 +44,7 @@ struct GatherArgs {
     const void *P;
     void *g;
     int64_t nB;
+    int64_t nslots;           // rows of P; nslots * B < 2^32 lets the batched gather index in 32 bits
 };
 
 struct MobArgs {
