@@ -1,0 +1,36 @@
+"""Host logic of bench.py: the algorithmic byte counts behind the roofline, the gate on
+the committed ncu traffic figures, and the CPU baseline of the paper's method."""
+import numpy as np
+
+import bench
+import posetgen as pg
+import paper_2211_13706_gb300 as mz
+
+
+def test_algorithmic_bytes_c2():
+    n, k, B, nnz = 1 << 20, 64, 1, 67098120
+    assert bench.algorithmic_bytes("niv_gather", n, k, B, nnz) == 4 * nnz + 4 * n + 8 * n
+    assert round(bench.algorithmic_bytes("niv_gather", n, k, B, nnz) / 1e6, 1) == 281.0
+    assert round(bench.algorithmic_bytes("mob_wave", n, k, B, nnz) / 1e6, 1) == 293.6
+    assert round(bench.algorithmic_bytes("chain_scan", n, k, B, nnz) / 1e6, 1) == 21.0
+    # every function column adds its own values, the map is read once
+    assert bench.algorithmic_bytes("niv_gather", n, k, 32, nnz) - bench.algorithmic_bytes("niv_gather", n, k, 1, nnz) \
+        == 8 * n * 31
+
+
+def test_traffic_figures_follow_the_kernel_sources():
+    v = bench.load_traffic("mob_wave", "c2", "f64")
+    assert v is not None and v > 2.9e8          # the committed capture matches these sources
+    assert bench.load_traffic("mob_wave", "c3", "f64") is None
+
+
+def test_cpu_paper_method_line():
+    p = pg.planted_chain_poset(3000, 12, 4, cross_deg=2)
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, host_only=True)
+    f = pg.function_values(p.n, 1, "i64:1048576", 2)[:, 0]
+    out = bench.cpu_paper_method(mz, plan, f, "i64")
+    assert out["kind"] == "paper_method_cpu" and out["check"]["moebius_of_zeta_is_f"]
+    assert out["one_core"]["threads"] == 1 and out["all_cores"]["value"] > 0
+    x = pg.function_values(p.n, 1, "f64u", 3)[:, 0]
+    z = bench.cpu_paper_method(mz, plan, x, "f64", gpu_g=np.zeros(p.n))
+    assert "zeta_vs_gpu_max_rel" in z["check"]
