@@ -18,10 +18,20 @@ def test_algorithmic_bytes_c2():
         == 8 * n * 31
 
 
-def test_traffic_figures_follow_the_kernel_sources():
-    v = bench.load_traffic("mob_wave", "c2", "f64")
-    assert v is not None and v > 2.9e8          # the committed capture matches these sources
+def test_traffic_figures_follow_the_kernel_sources(tmp_path, monkeypatch):
+    # the committed ncu figures count only while the kernel sources hash to their capture
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_2211_13706_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("mz_kernels.cu", "mz_arith.cuh"):
+        (csrc / f).write_bytes(open(f"{bench.ROOT}/paper_2211_13706_gb300/csrc/{f}", "rb").read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_source_hash()
+    (tmp_path / "profiles" / "ncu_traffic.txt").write_text(f"# c\nsource_hash: {h}\nmob_wave/c2/f64 = 123  # x\n")
+    assert bench.load_traffic("mob_wave", "c2", "f64") == 123.0
     assert bench.load_traffic("mob_wave", "c3", "f64") is None
+    (csrc / "mz_kernels.cu").write_bytes(b"changed")
+    assert bench.load_traffic("mob_wave", "c2", "f64") is None
 
 
 def test_cpu_paper_method_line():
