@@ -91,6 +91,21 @@ static void parallel_for(int64_t count, F fn) {
     for (auto &th : pool) th.join();
 }
 
+// Row order of the gather's tiles for a sparse map: rows by length, longest first (ties
+// in row order), so that a tile is about as wide as each of its rows. In slot order the
+// rows of the paper's random DAGs differ so much in length that padding the tiles to
+// their longest row reads 7-8 times nnz(N). The dense map keeps slot order.
+static std::vector<int32_t> sparse_tile_order(const int32_t *len, int64_t n) {
+    int32_t maxlen = 0;
+    for (int64_t r = 0; r < n; ++r) maxlen = std::max(maxlen, len[r]);
+    std::vector<int64_t> start((size_t)maxlen + 2, 0);
+    for (int64_t r = 0; r < n; ++r) start[(size_t)(maxlen - len[r]) + 1]++;
+    for (size_t l = 1; l < start.size(); ++l) start[l] += start[l - 1];
+    std::vector<int32_t> order((size_t)n);
+    for (int64_t r = 0; r < n; ++r) order[(size_t)start[(size_t)(maxlen - len[r])]++] = (int32_t)r;
+    return order;
+}
+
 // Device layouts of one side (all components): the concatenated slot map, the
 // tiled niv map for the zeta gather, and the map in Moebius processing order.
 static mz_status upload_side(mz_plan *p, int side) {
@@ -118,16 +133,21 @@ static mz_status upload_side(mz_plan *p, int side) {
     {   // tiles of 32 rows per component, column-major inside a tile
         std::vector<int64_t> toff;
         std::vector<int32_t> tk;
+        // rows at the tile positions of each sparse component (dense: position = row)
+        std::vector<std::vector<int32_t>> order(C);
+        for (size_t c = 0; c < C; ++c)
+            if (Hs[c].sparse) order[c] = sparse_tile_order(Hs[c].row_len.data(), Hs[c].n);
         size_t total = 0;
-        for (const HostSide &H : Hs) {
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
             const int64_t nt = (H.n + kTileRows - 1) / kTileRows;
             for (int64_t t = 0; t < nt; ++t) {
                 // dense: all k columns; sparse: as many as the tile's longest row, padded
                 int32_t kt = H.k;
                 if (H.sparse) {
                     kt = 1;
-                    for (int64_t r = t * kTileRows; r < std::min<int64_t>(H.n, (t + 1) * kTileRows); ++r)
-                        kt = std::max(kt, H.row_len[r]);
+                    for (int64_t q = t * kTileRows; q < std::min<int64_t>(H.n, (t + 1) * kTileRows); ++q)
+                        kt = std::max(kt, H.row_len[order[c][q]]);
                 }
                 toff.push_back((int64_t)total);
                 tk.push_back(kt);
@@ -152,9 +172,10 @@ static mz_status upload_side(mz_plan *p, int side) {
                 const HostSide &H = Hs[c];
                 const int64_t k = H.k;
                 const int32_t so = (int32_t)p->slot_off[c];
-                const int64_t r0 = rows ? u : 0, r1 = rows ? u + 1 : H.n;
-                for (int64_t r = r0; r < r1; ++r) {
-                    const int64_t t = tile0[c] + r / kTileRows, lane = r % kTileRows;
+                const int64_t q0 = rows ? u : 0, q1 = rows ? u + 1 : H.n;
+                for (int64_t q0i = q0; q0i < q1; ++q0i) {
+                    const int64_t r = H.sparse ? order[c][q0i] : q0i;    // the row at tile position q0i
+                    const int64_t t = tile0[c] + q0i / kTileRows, lane = q0i % kTileRows;
                     int32_t *dst = &tiled[(size_t)toff[t] + lane];
                     if (H.sparse) {           // finite entries only; the rest stay slot 0 (a zero slot)
                         int64_t q = 0;
@@ -497,18 +518,22 @@ static mz_status upload_side_device(mz_plan *p, int side) {
         D.ntiles = (n + kTileRows - 1) / kTileRows;
         std::vector<int64_t> toff((size_t)D.ntiles);
         std::vector<int32_t> tk((size_t)D.ntiles, (int32_t)k), rn((size_t)D.ntiles * kTileRows, -1);
+        std::vector<int32_t> order;   // sparse: the row at each tile position (as upload_side)
+        if (H.sparse) order = sparse_tile_order(rowcnt.data(), n);
         int64_t total = 0;
         for (int64_t t = 0; t < D.ntiles; ++t) {
             if (H.sparse) {   // as many columns as the tile's longest row
                 int32_t kt = 1;
-                for (int64_t r = t * kTileRows; r < std::min<int64_t>(n, (t + 1) * kTileRows); ++r)
-                    kt = std::max(kt, rowcnt[r]);
+                for (int64_t q = t * kTileRows; q < std::min<int64_t>(n, (t + 1) * kTileRows); ++q)
+                    kt = std::max(kt, rowcnt[order[q]]);
                 tk[t] = kt;
             }
             toff[t] = total;
             total += (int64_t)tk[t] * kTileRows;
         }
-        std::copy(H.row_node.begin(), H.row_node.end(), rn.begin());
+        for (int64_t q = 0; q < n; ++q) rn[q] = H.row_node[H.sparse ? order[q] : q];
+        int32_t *d_order = nullptr;
+        if (H.sparse && (st = tmp.put(&d_order, order.data(), order.size()))) return st;
         D.Nt = (int32_t *)plan_alloc(p, sizeof(int32_t) * (size_t)total);
         if (!D.Nt) {
             set_last_error("device allocation failed");
@@ -517,8 +542,8 @@ static mz_status upload_side_device(mz_plan *p, int side) {
         if ((st = upload(p, &D.tile_off, toff.data(), toff.size()))) return st;
         if ((st = upload(p, &D.tile_k, tk.data(), tk.size()))) return st;
         if ((st = upload(p, &D.row_node, rn.data(), rn.size()))) return st;
-        e = H.sparse ? launch_build_tiles_sparse(d_row_beg, d_rowcnt, d_pool, n, D.ntiles, D.tile_off, D.tile_k, D.Nt,
-                                                 p->num_sms, 0)
+        e = H.sparse ? launch_build_tiles_sparse(d_row_beg, d_rowcnt, d_pool, d_order, n, D.ntiles, D.tile_off,
+                                                 D.tile_k, D.Nt, p->num_sms, 0)
                      : launch_build_tiles(d_N, n, (int32_t)k, D.Nt, p->num_sms, 0);
         if (e != cudaSuccess) return cuda_fail(e, "tile build launch");
     }
@@ -1103,13 +1128,15 @@ mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *
                 e = cudaMemcpy(tk.data(), D.tile_k, sizeof(int32_t) * tk.size(), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
             const size_t total = D.ntiles ? (size_t)toff.back() + (size_t)tk.back() * kTileRows : 0;
-            std::vector<int32_t> t(total);
-            if ((e = cudaMemcpy(t.data(), D.Nt, sizeof(int32_t) * total, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            std::vector<int32_t> t(total), rn((size_t)D.ntiles * kTileRows);
+            if ((e = cudaMemcpy(t.data(), D.Nt, sizeof(int32_t) * total, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+                (e = cudaMemcpy(rn.data(), D.row_node, sizeof(int32_t) * rn.size(), cudaMemcpyDeviceToHost)) !=
+                    cudaSuccess)
                 return cuda_fail(e, "cudaMemcpy");
             // a tile row lists slots (every chain in order for a dense map, the finite
             // entries for a sparse one); zero slots stand for infinity
-            for (int64_t r = 0; r < n; ++r) {
-                const int64_t x = H.row_node[r], tt = r / kTileRows;
+            for (int64_t r = 0; r < n; ++r) {   // r: tile position, rn[r] its node
+                const int64_t x = rn[r], tt = r / kTileRows;
                 const int32_t *col = &t[(size_t)toff[tt] + r % kTileRows];
                 for (int64_t q = 0; q < tk[tt]; ++q) {
                     const int32_t y = H.slot_node[col[q * kTileRows]];

@@ -365,18 +365,20 @@ __global__ void __launch_bounds__(kBuildThreads) k_sparse_merge(SparseLevelArgs 
     }
 }
 
-// Sparse tiles: one warp per tile of 32 rows, lane = row; entries in slot order, then 0
-// (slot 0, a zero slot) up to the tile's row length.
+// Sparse tiles: one warp per tile of 32 positions, lane = position, order[position] =
+// its row; entries in slot order, then 0 (slot 0, a zero slot) up to the tile's width.
 __global__ void __launch_bounds__(kBuildThreads) k_build_tiles_sparse(const int64_t *row_beg, const int32_t *row_len,
-                                                                     const int32_t *pool, int64_t n, int64_t ntiles,
+                                                                     const int32_t *pool, const int32_t *order,
+                                                                     int64_t n, int64_t ntiles,
                                                                      const int64_t *tile_off, const int32_t *tile_k,
                                                                      int32_t *Nt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (kBuildThreads / 32);
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nwarps) {
-        const int64_t r = t * 32 + lane;
-        const int64_t b = r < n ? row_beg[r] : 0;
-        const int32_t len = r < n ? row_len[r] : 0;
+        const int64_t q = t * 32 + lane;
+        const int64_t r = q < n ? order[q] : 0;
+        const int64_t b = q < n ? row_beg[r] : 0;
+        const int32_t len = q < n ? row_len[r] : 0;
         int32_t *dst = Nt + tile_off[t] + lane;
         for (int32_t q = 0; q < tile_k[t]; ++q) dst[(int64_t)q * 32] = q < len ? pool[b + q] : 0;
     }
@@ -482,11 +484,11 @@ cudaError_t launch_sparse_merge(const SparseLevelArgs &a, int num_sms, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_tiles_sparse(const int64_t *row_beg, const int32_t *row_len, const int32_t *pool, int64_t n,
-                                      int64_t ntiles, const int64_t *tile_off, const int32_t *tile_k, int32_t *Nt,
-                                      int num_sms, cudaStream_t st) {
-    k_build_tiles_sparse<<<(unsigned)warp_blocks(ntiles, num_sms), kBuildThreads, 0, st>>>(row_beg, row_len, pool, n,
-                                                                                            ntiles, tile_off, tile_k, Nt);
+cudaError_t launch_build_tiles_sparse(const int64_t *row_beg, const int32_t *row_len, const int32_t *pool,
+                                      const int32_t *order, int64_t n, int64_t ntiles, const int64_t *tile_off,
+                                      const int32_t *tile_k, int32_t *Nt, int num_sms, cudaStream_t st) {
+    k_build_tiles_sparse<<<(unsigned)warp_blocks(ntiles, num_sms), kBuildThreads, 0, st>>>(
+        row_beg, row_len, pool, order, n, ntiles, tile_off, tile_k, Nt);
     return cudaGetLastError();
 }
 

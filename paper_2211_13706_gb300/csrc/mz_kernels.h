@@ -140,9 +140,9 @@ struct BuildMobSparseArgs {
 
 cudaError_t launch_sparse_bounds(const SparseLevelArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_sparse_merge(const SparseLevelArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_build_tiles_sparse(const int64_t *row_beg, const int32_t *row_len, const int32_t *pool, int64_t n,
-                                      int64_t ntiles, const int64_t *tile_off, const int32_t *tile_k, int32_t *Nt,
-                                      int num_sms, cudaStream_t st);
+cudaError_t launch_build_tiles_sparse(const int64_t *row_beg, const int32_t *row_len, const int32_t *pool,
+                                      const int32_t *order, int64_t n, int64_t ntiles, const int64_t *tile_off,
+                                      const int32_t *tile_k, int32_t *Nt, int num_sms, cudaStream_t st);
 cudaError_t launch_build_mob_rows_sparse(const BuildMobSparseArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_build_niv(const BuildNivArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_build_tiles(const int32_t *N, int64_t n, int32_t k, int32_t *Nt, int num_sms, cudaStream_t st);
