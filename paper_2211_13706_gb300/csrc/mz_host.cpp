@@ -12,9 +12,11 @@
 // With the device build only steps 1-4 and the heights run here; mz_build.cu
 // has the rest.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mz_internal.h"
@@ -22,6 +24,28 @@
 namespace mz {
 
 namespace {
+
+// Host threads for the level-parallel parts of the build: MZ_HOST_THREADS if set (tests
+// use 1 to compare with the one-thread order), else the hardware's, at most 64.
+int host_threads() {
+    const char *e = std::getenv("MZ_HOST_THREADS");
+    const int t = e ? std::atoi(e) : (int)std::thread::hardware_concurrency();
+    return std::max(1, std::min(64, t));
+}
+
+// Runs fn(thread, begin, end) over [0, count) in contiguous pieces, one per host
+// thread, when the range is large enough to pay for the threads; else inline.
+template <class F>
+void for_pieces(int64_t count, int nthreads, F fn) {
+    if (nthreads <= 1 || count < 4096) {
+        fn(0, (int64_t)0, count);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t)
+        pool.emplace_back([&, t]() { fn(t, count * t / nthreads, count * (t + 1) / nthreads); });
+    for (auto &th : pool) th.join();
+}
 
 // Hopcroft-Karp maximum matching between "upper" copies (edge sources) and
 // "lower" copies (edge targets) of the nodes (Alg. 1's bipartite graph G').
@@ -281,45 +305,98 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const s
             for (int64_t c = 0; c < k; ++c) H.nnz += row[c] != base32[c];
         }
     } else {
-        // scratch holds the merged row of the node being built; `touched` lists its chains
-        std::vector<int32_t> scratch(base32), touched;
+        // Level by level (heights): every child of a node sits on a lower level, so the
+        // nodes of one level merge their children's finished rows independently, on all
+        // host threads. Each thread keeps a scratch row (the merged row of the node it
+        // builds; `touched` lists its chains) and appends to its own entry buffers, which
+        // are concatenated after the level. A node that breaks its chain is recorded and
+        // the build goes on; the one reported is the one the sequential order (topological
+        // position, highest first) would meet first, whose descendants all passed.
+        std::vector<int32_t> height(n, 1);
+        for (int64_t i = n - 1; i >= 0; --i) {
+            const int32_t x = H.topo[i];
+            int32_t h = 0;
+            for (int64_t e = ptr[x]; e < ptr[x + 1]; ++e) h = std::max(h, height[adj[e]]);
+            height[x] = h + 1;
+        }
+        const int32_t nh = *std::max_element(height.begin(), height.end());
+        std::vector<int64_t> lstart((size_t)nh + 2, 0);
+        for (int64_t x = 0; x < n; ++x) lstart[height[x]]++;
+        for (size_t l = 1; l < lstart.size(); ++l) lstart[l] += lstart[l - 1];
+        std::vector<int32_t> by_level((size_t)n);
+        {
+            std::vector<int64_t> fill(lstart);
+            for (int64_t i = n - 1; i >= 0; --i) by_level[(size_t)fill[height[H.topo[i]] - 1]++] = H.topo[i];
+        }
         H.row_beg.assign(n, 0);
         H.row_len.assign(n, 0);
         H.ent_chain.clear();
         H.ent_slot.clear();
-        for (int64_t i = n - 1; i >= 0; --i) {
-            int32_t x = H.topo[i];
-            touched.clear();
-            kids.assign(adj.begin() + ptr[x], adj.begin() + ptr[x + 1]);
-            std::sort(kids.begin(), kids.end(), [&](int32_t a, int32_t b) { return pos[a] < pos[b]; });
-            for (int32_t z : kids) {
-                const int32_t cz = H.chain_id[z];
-                if (scratch[cz] >= H.node_slot[z]) continue;
-                const int64_t rz = H.node_slot[z] - cz - 1;
-                const int64_t b = H.row_beg[rz], e = b + H.row_len[rz];
-                for (int64_t q = b; q < e; ++q) {
-                    const int32_t c = H.ent_chain[q];
-                    if (scratch[c] == base32[c]) touched.push_back(c);
-                    scratch[c] = std::max(scratch[c], H.ent_slot[q]);
+        const int T = host_threads();
+        struct Local {
+            std::vector<int32_t> scratch, touched, kids, chain, slot;
+            std::vector<int64_t> rows;   // (row, first local entry, length) triples
+            int64_t bad = -1;            // largest topological position of a failing node
+        };
+        std::vector<Local> loc((size_t)T);
+        for (Local &L : loc) L.scratch = base32;
+        for (int32_t lv = 0; lv < nh; ++lv) {
+            const int64_t lo = lstart[lv], cnt = lstart[lv + 1] - lo;
+            for_pieces(cnt, T, [&](int t, int64_t b0, int64_t b1) {
+                Local &L = loc[(size_t)t];
+                L.chain.clear();
+                L.slot.clear();
+                L.rows.clear();
+                for (int64_t j = lo + b0; j < lo + b1; ++j) {
+                    const int32_t x = by_level[(size_t)j];
+                    L.touched.clear();
+                    L.kids.assign(adj.begin() + ptr[x], adj.begin() + ptr[x + 1]);
+                    std::sort(L.kids.begin(), L.kids.end(), [&](int32_t a, int32_t b) { return pos[a] < pos[b]; });
+                    for (int32_t z : L.kids) {
+                        const int32_t cz = H.chain_id[z];
+                        if (L.scratch[cz] >= H.node_slot[z]) continue;
+                        const int64_t rz = H.node_slot[z] - cz - 1;
+                        const int64_t b = H.row_beg[rz], e = b + H.row_len[rz];
+                        for (int64_t q = b; q < e; ++q) {
+                            const int32_t c = H.ent_chain[q];
+                            if (L.scratch[c] == base32[c]) L.touched.push_back(c);
+                            L.scratch[c] = std::max(L.scratch[c], H.ent_slot[q]);
+                        }
+                    }
+                    const int32_t cx = H.chain_id[x];
+                    const int32_t sx = H.node_slot[x];
+                    if (L.scratch[cx] != sx - 1) L.bad = std::max<int64_t>(L.bad, pos[x]);
+                    if (L.scratch[cx] == base32[cx]) L.touched.push_back(cx);
+                    L.scratch[cx] = sx;
+                    std::sort(L.touched.begin(), L.touched.end());
+                    L.rows.push_back(sx - cx - 1);
+                    L.rows.push_back((int64_t)L.chain.size());
+                    L.rows.push_back((int64_t)L.touched.size());
+                    for (int32_t c : L.touched) {
+                        L.chain.push_back(c);
+                        L.slot.push_back(L.scratch[c]);
+                        L.scratch[c] = base32[c];
+                    }
                 }
+            });
+            for (Local &L : loc) {   // append the level's rows in thread order
+                const int64_t off = (int64_t)H.ent_chain.size();
+                H.ent_chain.insert(H.ent_chain.end(), L.chain.begin(), L.chain.end());
+                H.ent_slot.insert(H.ent_slot.end(), L.slot.begin(), L.slot.end());
+                for (size_t q = 0; q < L.rows.size(); q += 3) {
+                    H.row_beg[L.rows[q]] = off + L.rows[q + 1];
+                    H.row_len[L.rows[q]] = (int32_t)L.rows[q + 2];
+                }
+                L.chain.clear();
+                L.slot.clear();
+                L.rows.clear();
             }
-            const int32_t cx = H.chain_id[x];
-            const int32_t sx = H.node_slot[x];
-            if (scratch[cx] != sx - 1) {
-                for (int32_t c : touched) scratch[c] = base32[c];
-                return bad_chain(cx, x);
-            }
-            if (scratch[cx] == base32[cx]) touched.push_back(cx);
-            scratch[cx] = sx;
-            std::sort(touched.begin(), touched.end());
-            const int64_t r = sx - cx - 1;
-            H.row_beg[r] = (int64_t)H.ent_chain.size();
-            H.row_len[r] = (int32_t)touched.size();
-            for (int32_t c : touched) {
-                H.ent_chain.push_back(c);
-                H.ent_slot.push_back(scratch[c]);
-                scratch[c] = base32[c];
-            }
+        }
+        int64_t bad = -1;
+        for (const Local &L : loc) bad = std::max(bad, L.bad);
+        if (bad >= 0) {
+            const int32_t x = H.topo[bad];
+            return bad_chain(H.chain_id[x], x);
         }
         H.nnz = (int64_t)H.ent_chain.size();
     }
@@ -332,12 +409,34 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const s
         int32_t h = 0;
         for (int64_t e = ptr[x]; e < ptr[x + 1]; ++e) h = std::max(h, H.level[adj[e]]);
         H.level[x] = h + 1;
-        const int32_t cx = H.chain_id[x];
-        int32_t u = 0;
-        H.for_row(H.node_slot[x] - cx - 1, [&](int32_t c, int32_t slot) {
-            if (c != cx) u = std::max(u, H.ulevel[H.slot_node[slot]] + 1);
-        });
-        H.ulevel[x] = u;
+    }
+    // U levels: one more than the largest U level among the other chains' entries, which
+    // all sit on lower heights; a sparse map's few, wide heights run on all host threads
+    {
+        auto ulevel_of = [&](int32_t x) {
+            const int32_t cx = H.chain_id[x];
+            int32_t u = 0;
+            H.for_row(H.node_slot[x] - cx - 1, [&](int32_t c, int32_t slot) {
+                if (c != cx) u = std::max(u, H.ulevel[H.slot_node[slot]] + 1);
+            });
+            H.ulevel[x] = u;
+        };
+        if (!H.sparse) {
+            for (int64_t i = n - 1; i >= 0; --i) ulevel_of(H.topo[i]);
+        } else {
+            const int32_t nh = *std::max_element(H.level.begin(), H.level.end());
+            std::vector<int64_t> lstart((size_t)nh + 2, 0);
+            for (int64_t x = 0; x < n; ++x) lstart[H.level[x]]++;
+            for (size_t l = 1; l < lstart.size(); ++l) lstart[l] += lstart[l - 1];
+            std::vector<int32_t> by_level((size_t)n);
+            std::vector<int64_t> fill(lstart);
+            for (int64_t x = 0; x < n; ++x) by_level[(size_t)fill[H.level[x] - 1]++] = (int32_t)x;
+            const int T = host_threads();
+            for (int32_t lv = 0; lv < nh; ++lv)
+                for_pieces(lstart[lv + 1] - lstart[lv], T, [&](int, int64_t b0, int64_t b1) {
+                    for (int64_t j = lstart[lv] + b0; j < lstart[lv] + b1; ++j) ulevel_of(by_level[(size_t)j]);
+                });
+        }
     }
     H.nlevels = *std::max_element(H.level.begin(), H.level.end());
     H.nulevels = *std::max_element(H.ulevel.begin(), H.ulevel.end()) + 1;

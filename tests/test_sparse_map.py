@@ -101,3 +101,30 @@ def test_er_paper_scale_sampled(degree):
     assert (gg[rows] == oracle.zeta_rows(p.n, p.src, p.dst, f, rows)).all()
     res, _ = oracle.mobius_residual_rows(p.n, p.src, p.dst, y.cpu().numpy(), f, rows)
     assert all(int(v) % (1 << 64) == 0 for v in res)
+
+
+def test_sparse_host_build_threads_agree(monkeypatch):
+    # levels of >= 4096 nodes run on several host threads; the plan must not depend on it
+    p = pg.er_dag(150000, 6, 8)
+    plans = {}
+    for t in ("1", "4"):
+        monkeypatch.setenv("MZ_HOST_THREADS", t)
+        plans[t] = mz.Plan(p.n, p.src, p.dst, None, host_only=True, niv_format=2)
+    a, b = plans["1"], plans["4"]
+    for key in ("k", "nnz", "levels", "ulevels"):
+        assert a.info[key] == b.info[key], key
+    for w in (mz.MZ_EXPORT_ULEVEL, mz.MZ_EXPORT_LEVEL, mz.MZ_EXPORT_CHAIN_ID):
+        assert np.array_equal(a.export(w), b.export(w))
+    # a broken chain is reported at the same node either way
+    cid = a.export(mz.MZ_EXPORT_CHAIN_ID).copy()
+    lvl = a.export(mz.MZ_EXPORT_LEVEL)
+    x = int(np.flatnonzero(lvl == 5)[0])
+    cid[x] = cid[int(np.flatnonzero(lvl == 9)[0])]
+    msgs = []
+    for t in ("1", "4"):
+        monkeypatch.setenv("MZ_HOST_THREADS", t)
+        with pytest.raises(mz.MzError) as e:
+            mz.Plan(p.n, p.src, p.dst, cid, host_only=True, niv_format=2)
+        assert e.value.status == mz.MZ_ERR_BAD_CHAINS
+        msgs.append(str(e.value))
+    assert msgs[0] == msgs[1]
