@@ -47,18 +47,72 @@ void for_pieces(int64_t count, int nthreads, F fn) {
     for (auto &th : pool) th.join();
 }
 
-// Hopcroft-Karp maximum matching between "upper" copies (edge sources) and
-// "lower" copies (edge targets) of the nodes (Alg. 1's bipartite graph G').
+// Maximum matching between "upper" copies (edge sources) and "lower" copies (edge
+// targets) of the nodes (Alg. 1's bipartite graph G'): a Karp-Sipser start (Karp and
+// Sipser 1981), then Hopcroft-Karp phases (Hopcroft and Karp 1973) until no augmenting
+// path is left. On the paper's random DAGs the start is already maximum.
 // Returns next_of[u] = the node matched below u, or -1.
 std::vector<int32_t> max_matching(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int32_t> &adj) {
     const int32_t NIL = -1;
     std::vector<int32_t> mate_u(n, NIL), mate_v(n, NIL), dist(n), queue(n);
     std::vector<int64_t> it(n);
     std::vector<int32_t> stack;
-    // greedy start
-    for (int64_t u = 0; u < n; ++u)
-        for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e)
-            if (mate_v[adj[e]] == NIL) { mate_u[u] = adj[e]; mate_v[adj[e]] = (int32_t)u; break; }
+    // Karp-Sipser start: match vertices left with one free neighbour first (such an edge is in
+    // some maximum matching), else any free edge; the phases below then finish the job.
+    {
+        std::vector<int64_t> pptr(n + 1, 0);
+        for (int64_t e = 0; e < (int64_t)adj.size(); ++e) pptr[adj[e] + 1]++;
+        for (int64_t v = 0; v < n; ++v) pptr[v + 1] += pptr[v];
+        std::vector<int32_t> padj(adj.size());
+        {
+            std::vector<int64_t> fill(pptr.begin(), pptr.end() - 1);
+            for (int64_t u = 0; u < n; ++u)
+                for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e) padj[fill[adj[e]]++] = (int32_t)u;
+        }
+        std::vector<int32_t> deg_u(n), deg_v(n);
+        for (int64_t u = 0; u < n; ++u) deg_u[u] = (int32_t)(ptr[u + 1] - ptr[u]);
+        for (int64_t v = 0; v < n; ++v) deg_v[v] = (int32_t)(pptr[v + 1] - pptr[v]);
+        std::vector<int64_t> one;   // degree-1 vertices: u as u, v as -(v + 1)
+        for (int64_t u = 0; u < n; ++u) if (deg_u[u] == 1) one.push_back(u);
+        for (int64_t v = 0; v < n; ++v) if (deg_v[v] == 1) one.push_back(-(v + 1));
+        auto take = [&](int32_t u, int32_t v) {   // match u-v, remove both, update degrees
+            mate_u[u] = v;
+            mate_v[v] = u;
+            for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e) {
+                const int32_t w = adj[e];
+                if (mate_v[w] == NIL && --deg_v[w] == 1) one.push_back(-(int64_t)w - 1);
+            }
+            for (int64_t e = pptr[v]; e < pptr[v + 1]; ++e) {
+                const int32_t w = padj[e];
+                if (mate_u[w] == NIL && --deg_u[w] == 1) one.push_back(w);
+            }
+        };
+        int64_t next_u = 0;
+        while (true) {
+            while (!one.empty()) {
+                const int64_t t = one.back();
+                one.pop_back();
+                if (t >= 0) {
+                    const int32_t u = (int32_t)t;
+                    if (mate_u[u] != NIL || deg_u[u] != 1) continue;
+                    for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e)
+                        if (mate_v[adj[e]] == NIL) { take(u, adj[e]); break; }
+                } else {
+                    const int32_t v = (int32_t)(-t - 1);
+                    if (mate_v[v] != NIL || deg_v[v] != 1) continue;
+                    for (int64_t e = pptr[v]; e < pptr[v + 1]; ++e)
+                        if (mate_u[padj[e]] == NIL) { take(padj[e], v); break; }
+                }
+            }
+            // no degree-1 vertex left: one greedy edge, then look again
+            while (next_u < n && (mate_u[next_u] != NIL || deg_u[next_u] == 0)) ++next_u;
+            if (next_u >= n) break;
+            bool any = false;
+            for (int64_t e = ptr[next_u]; e < ptr[next_u + 1]; ++e)
+                if (mate_v[adj[e]] == NIL) { take((int32_t)next_u, adj[e]); any = true; break; }
+            if (!any) deg_u[next_u] = 0;
+        }
+    }
     const int32_t INF = INT32_MAX;
     while (true) {
         // BFS from free upper nodes over alternating paths
