@@ -808,6 +808,7 @@ static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, c
         std::vector<std::thread> pool;
         for (int32_t t = 0; t < nthreads; ++t)
             pool.emplace_back([&]() {
+                set_host_threads_cap(1);   // the posets already share the host's threads
                 for (int32_t c = next++; c < count; c = next++) work(c);
             });
         for (auto &th : pool) th.join();

@@ -25,11 +25,15 @@ namespace mz {
 
 namespace {
 
-// Host threads for the level-parallel parts of the build: MZ_HOST_THREADS if set (tests
-// use 1 to compare with the one-thread order), else the hardware's, at most 64.
+thread_local int t_threads_cap = 0;   // set by callers that already run builds in parallel
+
+// Host threads for the parallel parts of the build: MZ_HOST_THREADS if set (tests use 1
+// to compare with the one-thread order), else the hardware's, at most 64; 1 inside a
+// build that already runs on one of several threads (many posets at once).
 int host_threads() {
     const char *e = std::getenv("MZ_HOST_THREADS");
-    const int t = e ? std::atoi(e) : (int)std::thread::hardware_concurrency();
+    int t = e ? std::atoi(e) : (int)std::thread::hardware_concurrency();
+    if (t_threads_cap > 0) t = std::min(t, t_threads_cap);
     return std::max(1, std::min(64, t));
 }
 
@@ -171,6 +175,8 @@ std::vector<int32_t> max_matching(int64_t n, const std::vector<int64_t> &ptr, co
 
 }  // namespace
 
+void set_host_threads_cap(int cap) { t_threads_cap = cap; }
+
 mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const std::vector<int32_t> &dst_in,
                           const int32_t *chain_in, int niv_format, bool device_niv, HostSide &H, std::string &err) {
     H = HostSide();
@@ -195,18 +201,29 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const s
         std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
         for (int64_t i = 0; i < m; ++i) adj[fill[src_in[i]]++] = dst_in[i];
     }
-    {   // sort + unique each child list, compact
-        int64_t w = 0;
-        for (int64_t x = 0; x < n; ++x) {
-            int64_t b = ptr[x], e = ptr[x + 1];
-            std::sort(adj.begin() + b, adj.begin() + e);
-            int64_t start = w;
-            for (int64_t i = b; i < e; ++i)
-                if (i == b || adj[i] != adj[i - 1]) adj[w++] = adj[i];
-            ptr[x] = start;
-        }
-        ptr[n] = w;
-        adj.resize(w);
+    {   // sort each child list and count its distinct children (in parallel over nodes),
+        // then compact
+        std::vector<int64_t> uptr(n + 1, 0);
+        for_pieces(n, host_threads(), [&](int, int64_t x0, int64_t x1) {
+            for (int64_t x = x0; x < x1; ++x) {
+                const int64_t b = ptr[x], e = ptr[x + 1];
+                std::sort(adj.begin() + b, adj.begin() + e);
+                int64_t u = 0;
+                for (int64_t i = b; i < e; ++i) u += (i == b || adj[i] != adj[i - 1]);
+                uptr[x + 1] = u;
+            }
+        });
+        for (int64_t x = 0; x < n; ++x) uptr[x + 1] += uptr[x];
+        std::vector<int32_t> uadj((size_t)uptr[n]);
+        for_pieces(n, host_threads(), [&](int, int64_t x0, int64_t x1) {
+            for (int64_t x = x0; x < x1; ++x) {
+                int64_t w = uptr[x];
+                for (int64_t i = ptr[x]; i < ptr[x + 1]; ++i)
+                    if (i == ptr[x] || adj[i] != adj[i - 1]) uadj[(size_t)w++] = adj[i];
+            }
+        });
+        ptr.swap(uptr);
+        adj.swap(uadj);
     }
     H.edges = (int64_t)adj.size();
 

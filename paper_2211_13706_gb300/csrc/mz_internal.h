@@ -132,4 +132,8 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src, const std:
 
 void set_last_error(const std::string &s);
 
+// Caps the host threads build_host_side uses on the calling thread (0: no cap); set to 1
+// where several posets are built at once, one per thread.
+void set_host_threads_cap(int cap);
+
 }  // namespace mz
