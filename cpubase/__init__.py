@@ -45,6 +45,7 @@ def _load():
         for suf in ("f64", "i64"):
             getattr(lib, f"mzcpu_zeta_{suf}").argtypes = [i64, i32, vp, vp, vp, vp, vp, vp]
             getattr(lib, f"mzcpu_mobius_{suf}").argtypes = [i64, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp]
+            getattr(lib, f"mzcpu_mobius_u_{suf}").argtypes = [i64, i64, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -60,7 +61,7 @@ def set_threads(t: int) -> None:
 class CpuPlan:
     """Host arrays of the paper's method for one poset, from a plan's exports (dense niv map)."""
 
-    def __init__(self, plan, export_niv, export_chain_id, export_chain_pos, export_level):
+    def __init__(self, plan, export_niv, export_chain_id, export_chain_pos, export_level, export_ulevel=None):
         info = plan.info
         self.n, self.k = int(info["n"]), int(info["k"])
         n, k = self.n, self.k
@@ -82,6 +83,13 @@ class CpuPlan:
         counts = np.bincount(level)[1:]
         self.nlevels = int(counts.size)
         self.lvl_ptr = np.ascontiguousarray(np.concatenate([[0], np.cumsum(counts)]).astype(np.int64))
+        self.u_nodes = self.u_ptr = None
+        if export_ulevel is not None:   # levels of U's dependency graph, from 0
+            ul = plan.export(export_ulevel).astype(np.int64)
+            self.u_nodes = np.ascontiguousarray(np.argsort(ul, kind="stable").astype(np.int32))
+            uc = np.bincount(ul)
+            self.n_ulevels = int(uc.size)
+            self.u_ptr = np.ascontiguousarray(np.concatenate([[0], np.cumsum(uc)]).astype(np.int64))
         self.P = None
 
     def _ptr(self, a):
@@ -100,6 +108,17 @@ class CpuPlan:
         getattr(_load(), f"mzcpu_zeta_{suf}")(self.n, self.k, self._ptr(self.chain_base), self._ptr(self.slot_node),
                                                self._ptr(self.N), self._ptr(f), self._ptr(g), self._ptr(P))
         return g
+
+    def mobius_u(self, g):
+        """Moebius with U's dependency levels as the schedule (needs export_ulevel)."""
+        g, suf, dt = self._prep(g)
+        f = np.empty(self.n, dt)
+        P = np.empty(self.S, dt)
+        getattr(_load(), f"mzcpu_mobius_u_{suf}")(self.n, self.S, self.k, self._ptr(self.node_slot),
+                                                   self._ptr(self.chain_of), self._ptr(self.N), self._ptr(self.u_ptr),
+                                                   self.n_ulevels, self._ptr(self.u_nodes), self._ptr(g), self._ptr(f),
+                                                   self._ptr(P))
+        return f
 
     def mobius(self, g):
         g, suf, dt = self._prep(g)

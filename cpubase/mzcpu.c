@@ -19,6 +19,8 @@
  *   a level in parallel: f(x) = g(x) - P[slot(x) - 1] - sum_{c != chain(x)} P[N(x, c)],
  *   then P[slot(x)] = P[slot(x) - 1] + f(x). A level is an antichain, and every slot
  *   x reads belongs to a lower level.
+ * mzcpu_mobius_u_* runs Alg. 4's two loops instead, the first in the order of the levels
+ * of U's dependency graph (the library's default schedule, with barriers between levels).
  * The int64 variant computes modulo 2^64 (unsigned arithmetic on the same bits).
  */
 #include <stdint.h>
@@ -87,5 +89,32 @@ void mzcpu_set_threads(int t) {
         }                                                                                               \
     }
 
+/* Moebius in the order of U's own dependency levels (fewer levels than antichains):
+ * level by level, y'(x) = g(x) - sum_{c != chain(x)} P[N(x, c)] into P[slot(x)] (the
+ * first loop of Alg. 4), then f(x) = P[slot(x)] - P[slot(x) - 1] for all x (V^-1). */
+#define MZCPU_DEFINE_U(T, SUF)                                                                          \
+    void mzcpu_mobius_u_##SUF(int64_t n, int64_t S, int32_t k, const int32_t *node_slot,               \
+                              const int32_t *chain_of, const int32_t *N, const int64_t *lvl_ptr,        \
+                              int32_t nlevels, const int32_t *lvl_nodes, const T *g, T *f, T *P) {      \
+        int64_t s, x;                                                                                   \
+        _Pragma("omp parallel for schedule(static)") for (s = 0; s < S; ++s) P[s] = 0;                 \
+        _Pragma("omp parallel") for (int32_t l = 0; l < nlevels; ++l) {                                \
+            int64_t i;                                                                                  \
+            _Pragma("omp for schedule(static)") for (i = lvl_ptr[l]; i < lvl_ptr[l + 1]; ++i) {         \
+                const int32_t y = lvl_nodes[i];                                                         \
+                const int32_t cy = chain_of[y];                                                         \
+                const int32_t *row = N + (int64_t)y * k;                                                \
+                T acc = g[y];                                                                           \
+                for (int32_t j = 0; j < k; ++j)                                                         \
+                    if (j != cy) acc -= P[row[j]];                                                      \
+                P[node_slot[y]] = acc;                                                                  \
+            }                                                                                           \
+        }                                                                                               \
+        _Pragma("omp parallel for schedule(static)") for (x = 0; x < n; ++x)                           \
+            f[x] = P[node_slot[x]] - P[node_slot[x] - 1];                                               \
+    }
+
 MZCPU_DEFINE(double, f64)
 MZCPU_DEFINE(uint64_t, i64)
+MZCPU_DEFINE_U(double, f64)
+MZCPU_DEFINE_U(uint64_t, i64)

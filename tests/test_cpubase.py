@@ -12,7 +12,7 @@ import paper_2211_13706_gb300 as mz
 def _cpu_plan(p, cid):
     plan = mz.Plan(p.n, p.src, p.dst, cid, host_only=True, niv_format=1)
     return cpubase.CpuPlan(plan, mz.MZ_EXPORT_NIV, mz.MZ_EXPORT_CHAIN_ID, mz.MZ_EXPORT_CHAIN_POS,
-                           mz.MZ_EXPORT_LEVEL)
+                           mz.MZ_EXPORT_LEVEL, mz.MZ_EXPORT_ULEVEL)
 
 
 @pytest.mark.parametrize("maker", [
@@ -29,6 +29,7 @@ def test_cpu_baseline_matches_oracle(maker):
     g = cp.zeta(f)
     assert np.array_equal(g, oracle.zeta(Z, f))
     assert np.array_equal(cp.mobius(g), f)
+    assert np.array_equal(cp.mobius_u(g), f)          # U-level schedule, same exact result
     h = pg.function_values(p.n, 1, "i64:1000", 6)[:, 0]
     assert np.array_equal(cp.zeta(cp.mobius(h)), h)
     x = pg.function_values(p.n, 1, "f64u", 7)[:, 0]
