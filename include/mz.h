@@ -231,8 +231,11 @@ mz_status mz_mobius(const mz_plan *plan, mz_dtype dtype, const void *g, void *f,
  * 16 MiB), which every GPU that loads the library holds until the process exits.
  * The call allocates nothing: it needs no workspace argument, and the plan must
  * already exist (mz_build can route its own buffers through opts->dev_alloc).
- * The first call on each device looks up the array's device address, so make that
- * first call before any stream capture.
+ * The first call in each CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it for that context, so make that first call
+ * before any stream capture. A context that is destroyed and created again (for
+ * example after cudaDeviceReset) is a new context: its first call looks the address
+ * up again, and its array starts with undefined contents.
  *   f, g, batch, stream  as for mz_zeta
  * Returns MZ_ERR_INVALID_ARG when the transform needs more scratch than the fixed
  * array holds (the needed bytes are mz_workspace_size(plan, dtype, batch)), and the
@@ -266,7 +269,7 @@ mz_status mz_check(const mz_plan *plan, mz_stream stream);
    value). An autotuner times transforms under candidate shapes and keeps the best. */
 typedef struct {
     int32_t mobius_blocks_per_sm; /* as mz_build_opts::mobius_blocks_per_sm (default 2) */
-    int32_t mobius_pace_ns;       /* as mz_build_opts::mobius_pace_ns (default 1000; < 0 = none) */
+    int32_t mobius_pace_ns;       /* as mz_build_opts::mobius_pace_ns (default 500; < 0 = none) */
     int32_t gather_blocks_per_sm; /* resident 256-thread blocks per SM of the zeta gather (default 32) */
     int32_t reserved;
 } mz_tuning;

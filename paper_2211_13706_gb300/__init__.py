@@ -61,11 +61,28 @@ _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
 def _torch_alloc(nbytes, ctx):
+    """dev_alloc callback. Only an allocation failure (torch.cuda.OutOfMemoryError)
+    becomes NULL, which the library reports as MZ_ERR_OOM; any other error is kept in
+    _ALLOC_ERRORS and also returns NULL (an exception cannot cross the C boundary),
+    and the binding re-raises it after the failed build instead of reporting OOM."""
+    import torch
     try:
-        import torch
         return torch.cuda.caching_allocator_alloc(int(nbytes))
-    except Exception:       # NULL: the library reports MZ_ERR_OOM
+    except torch.cuda.OutOfMemoryError:
         return None
+    except BaseException as exc:   # noqa: BLE001  (re-raised by _check_alloc_errors)
+        _ALLOC_ERRORS.append(exc)
+        return None
+
+
+_ALLOC_ERRORS: list = []
+
+
+def _check_alloc_errors():
+    if _ALLOC_ERRORS:
+        exc = _ALLOC_ERRORS[0]
+        _ALLOC_ERRORS.clear()
+        raise RuntimeError(f"device allocation callback failed: {exc!r}") from exc
 
 
 def _torch_free(ptr, ctx):
@@ -169,6 +186,8 @@ def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, 
     out = ctypes.c_void_p()
     st = lib.mz_build(int(n), int(src.size), src.ctypes.data, dst.ctypes.data,
                       None if cid is None else cid.ctypes.data, ctypes.byref(opts), ctypes.byref(out))
+    if st != MZ_OK:
+        _check_alloc_errors()
     _check(st, "mz_build")
     return out.value
 
@@ -191,6 +210,8 @@ def mz_build_batch(posets, *, build_transpose: bool = False, host_only: bool = F
     out = ctypes.c_void_p()
     st = lib.mz_build_batch(count, ns.ctypes.data, ms.ctypes.data, psrc, pdst,
                             None if all(c is None for c in cids) else pcid, ctypes.byref(opts), ctypes.byref(out))
+    if st != MZ_OK:
+        _check_alloc_errors()
     _check(st, "mz_build_batch")
     return out.value
 
@@ -214,8 +235,20 @@ def mz_zeta(plan, dtype, f_ptr, g_ptr, batch, ws_ptr, ws_bytes, stream=0):
     _transform("mz_zeta", plan, dtype, f_ptr, g_ptr, batch, ws_ptr, ws_bytes, stream)
 
 
+def _header_scratch_bytes() -> int:
+    """MZ_NOALLOC_SCRATCH_BYTES as include/mz.h defines it (the header the library is
+    compiled from), so that the binding cannot drift from the library."""
+    import re
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "include", "mz.h")
+    with open(path) as fh:
+        m = re.search(r"#define\s+MZ_NOALLOC_SCRATCH_BYTES\s+\(\(size_t\)(\d+)\s*<<\s*(\d+)\)", fh.read())
+    if not m:
+        raise RuntimeError("MZ_NOALLOC_SCRATCH_BYTES not found in include/mz.h")
+    return int(m.group(1)) << int(m.group(2))
+
+
 # Bytes of the library's fixed scratch array used by mz_zeta_noalloc.
-MZ_NOALLOC_SCRATCH_BYTES = 16 << 20
+MZ_NOALLOC_SCRATCH_BYTES = _header_scratch_bytes()
 
 
 def mz_zeta_noalloc(plan, dtype, f_ptr, g_ptr, batch, stream=0):

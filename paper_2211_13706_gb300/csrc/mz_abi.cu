@@ -966,10 +966,68 @@ mz_status mz_zeta(const mz_plan *plan, mz_dtype dtype, const void *f, void *g, i
 // ---------------------------------------------------------------- zeta without allocation
 // Scratch for mz_zeta_noalloc: a fixed device array owned by the library. Its
 // name is only a host-side handle; the device address comes from
-// cudaGetSymbolAddress, looked up once per device on the first call there.
+// cudaGetSymbolAddress in the context that is current at the call. The address
+// is cached per CUDA context, keyed by the context's process-unique id
+// (cuCtxGetId, reached through the runtime's driver entry points so that the
+// library needs no link against the driver), so a context that was destroyed
+// and created again (cudaDeviceReset) gets a fresh lookup instead of a stale
+// address.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MZ_NOALLOC_SCRATCH_BYTES];
-static void *g_noalloc_addr[128];
+struct NoallocEntry {
+    unsigned long long ctx_id;
+    void *addr;
+};
+static NoallocEntry g_noalloc_cache[64];
+static int g_noalloc_used = 0, g_noalloc_next = 0;
 static std::mutex g_noalloc_mutex;
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+static CtxGetCurrentFn g_ctx_get_current = nullptr;
+static CtxGetIdFn g_ctx_get_id = nullptr;
+static bool g_ctx_fns_tried = false;
+
+// Id of the context current on this thread; false if it cannot be had.
+static bool current_context_id(unsigned long long *id) {
+    if (!g_ctx_fns_tried) {
+        g_ctx_fns_tried = true;
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess && qb == cudaDriverEntryPointSuccess) {
+            g_ctx_get_current = (CtxGetCurrentFn)a;
+            g_ctx_get_id = (CtxGetIdFn)b;
+        }
+        cudaGetLastError();
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return false;
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return false;
+    return g_ctx_get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array in the current context.
+static mz_status noalloc_address(void **out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
+    if (have_id)
+        for (int i = 0; i < g_noalloc_used; ++i)
+            if (g_noalloc_cache[i].ctx_id == id) {
+                *out = g_noalloc_cache[i].addr;
+                return MZ_OK;
+            }
+    void *addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);   // also makes the context current
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    if (!have_id) have_id = current_context_id(&id);
+    if (have_id) {   // no id (no driver entry points): look the address up on every call
+        const int slot = g_noalloc_used < 64 ? g_noalloc_used++ : (g_noalloc_next++ & 63);
+        g_noalloc_cache[slot] = {id, addr};
+    }
+    *out = addr;
+    return MZ_OK;
+}
 
 mz_status mz_zeta_noalloc(const mz_plan *plan, mz_dtype dtype, const void *f, void *g, int32_t batch,
                           mz_stream stream) {
@@ -991,22 +1049,13 @@ mz_status mz_zeta_noalloc(const mz_plan *plan, mz_dtype dtype, const void *f, vo
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 128) {
-        set_last_error("device index out of range");
+    if (dev != plan->device) {
+        set_last_error("the current CUDA device is not the plan's device");
         return MZ_ERR_INVALID_ARG;
     }
     void *ws = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_addr[dev]) {
-            e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_noalloc_addr[dev] = nullptr;
-                return cuda_fail(e, "cudaGetSymbolAddress");
-            }
-        }
-        ws = g_noalloc_addr[dev];
-    }
+    mz_status st = noalloc_address(&ws);
+    if (st) return st;
     return run_zeta(plan, 0, dtype, f, g, batch, ws, MZ_NOALLOC_SCRATCH_BYTES, stream);
 }
 

@@ -76,3 +76,26 @@ def test_noalloc_batched_and_size_limit():
         mz.mz_zeta_noalloc(plan.handle, mz.MZ_I64, x.data_ptr(), y.data_ptr(), big, stream)
     assert e.value.status == mz.MZ_ERR_INVALID_ARG
     assert "scratch" in str(e.value)
+
+
+def test_noalloc_at_the_size_limit():
+    """The largest batch whose workspace (mz_workspace_size) fits the fixed array runs and
+    matches mz_zeta exactly; one more column does not fit and is refused."""
+    p = pg.planted_chain_poset(4096, 16, 4, cross_p=4 / 4096)
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id)
+    limit = mz.MZ_NOALLOC_SCRATCH_BYTES
+    fits = [b for b in range(1, 4096) if mz.mz_workspace_size(plan.handle, mz.MZ_I64, b) <= limit]
+    bmax = max(fits)
+    assert mz.mz_workspace_size(plan.handle, mz.MZ_I64, bmax + 1) > limit
+    stream = torch.cuda.current_stream().cuda_stream
+    for b, ok in ((bmax, True), (bmax + 1, False)):
+        f = _device_values(p.n, b, mz.MZ_I64, 5)
+        got = torch.empty_like(f)
+        if ok:
+            mz.mz_zeta_noalloc(plan.handle, mz.MZ_I64, f.data_ptr(), got.data_ptr(), b, stream)
+            mz.mz_check(plan.handle, stream)
+            assert torch.equal(got, plan.zeta(f))
+        else:
+            with pytest.raises(mz.MzError) as e:
+                mz.mz_zeta_noalloc(plan.handle, mz.MZ_I64, f.data_ptr(), got.data_ptr(), b, stream)
+            assert e.value.status == mz.MZ_ERR_INVALID_ARG
