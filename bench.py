@@ -163,6 +163,9 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:   # sampling has begun before the timed steps
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -200,25 +203,32 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- device arm
-def algorithmic_bytes(kernel: str, n: int, k: int, B: int, nnz: int) -> int:
+def algorithmic_bytes(kernel: str, n: int, k: int, B: int, nnz: int, wave=None) -> int:
     """Bytes a launch must move: the finite entries of the niv map it needs (nnz(N), or
     nnz(N) - n without the own-chain entries), its inputs and its outputs; the prefix
-    array y' counts only where a kernel writes it or reads it as its own input."""
+    array y' counts only where a kernel writes it or reads it as its own input.
+    wave = (rows, entries): the rows of the Moebius forward substitution and their finite
+    entries on other chains (U-level schedule: the rows another chain reads; None: all
+    rows, as in the antichain schedule)."""
+    wr, we = wave if wave is not None else (n, nnz - n)
     if kernel == "chain_scan":
         return 8 * n * B + 4 * (n + k) + 8 * (n + k) * B
     if kernel == "niv_gather":
         return 4 * nnz + 4 * n + 8 * n * B
     if kernel == "mob_init":
-        return 4 * (n + k) + 8 * (n + k) * B
+        return (n + k) + 4 * (n + k) + 8 * (n + k) * B
     if kernel == "mob_wave":
-        return 4 * (nnz - n) + 12 * n + 8 * n * B + 8 * n * B
+        return 4 * we + 12 * wr + 8 * wr * B + 8 * wr * B
+    if kernel == "mob_leaf":
+        leaves = n - wr
+        return 4 * nnz + 8 * n + 8 * leaves * B + 8 * leaves * B
     if kernel == "mob_diff":
         return 4 * (n + k) + 8 * (n + k) * B + 8 * n * B
     raise KeyError(kernel)
 
 
 ZETA_KERNELS = ["chain_scan", "niv_gather"]
-MOB_KERNELS = ["mob_init", "mob_wave", "mob_diff"]
+MOB_KERNELS = ["mob_init", "mob_wave", "mob_leaf", "mob_diff"]
 MOB_KERNELS_ANTI = ["mob_init", "mob_wave"]
 
 
@@ -343,6 +353,73 @@ def cpu_baseline(p, f_np, budget_s: float, max_rows: int):
                       "the oracle's Moebius has no per-row form cheaper than O(|out(x)|^2)"}
 
 
+def _as_f64(v):
+    return v[0].astype(np.float64) + v[1].astype(np.float64) if isinstance(v, tuple) else np.asarray(v, np.float64)
+
+
+def oracle_row_errors(p, outs, rows):
+    """Per-result error of GPU results against the oracle (exact sums, correctly rounded)
+    on the listed rows. outs: {dtype: (f, g, m)}: the input f, the GPU's zeta g = Z f and
+    the GPU's Moebius m = M g of that g, each fp64 or an F32C (hi, lo) pair. Returns per
+    dtype the largest componentwise error of zeta, |g(x) - (Z f)(x)| / (Z|f|)(x), and of
+    the Moebius residual, |(Z m)(x) - g(x)| / ((Z|m|)(x) + |g(x)|) (its backward error)."""
+    import oracle
+    tiny = np.finfo(np.float64).tiny
+    res = {}
+    for dk, (f, g, m) in outs.items():
+        ref = oracle.zeta_rows(p.n, p.src, p.dst, f, rows)
+        fa = (np.abs(f[0]), np.abs(f[1])) if isinstance(f, tuple) else np.abs(f)
+        mag = oracle.zeta_rows(p.n, p.src, p.dst, fa, rows)
+        ez = np.abs(_as_f64(g)[rows] - np.asarray(ref, np.float64)) / np.maximum(np.asarray(mag, np.float64), tiny)
+        res[dk] = {"zeta_max_rel": float(ez.max())}
+        # The Moebius transform of rounded data grows like 10^(0.23 U-levels) on these posets
+        # for any algorithm; where that overflows the output type there is no residual to take.
+        if np.all(np.isfinite(_as_f64(m))):
+            r, rm = oracle.mobius_residual_rows(p.n, p.src, p.dst, m, g, rows)
+            em = np.abs(np.asarray(r, np.float64)) / np.maximum(np.asarray(rm, np.float64), tiny)
+            res[dk]["mobius_residual_max_rel"] = float(em.max())
+            res[dk]["mobius_max_abs"] = float(np.max(np.abs(_as_f64(m))))
+        else:
+            res[dk]["mobius_residual_max_rel"] = None
+            res[dk]["mobius_overflow"] = True
+    return res
+
+
+def accuracy_leg(cases, budget_s: float):
+    """The CPU-baseline leg's second product: the GPU results of each case checked against
+    the oracle on sampled rows, case after case until the time budget is spent (every
+    case gets at least one row). cases: list of (name, poset, outs, n_rows)."""
+    t0 = time.perf_counter()
+    out = {}
+    for name, p, outs, n_rows in cases:
+        rows = np.random.default_rng(7).choice(p.n, min(n_rows, p.n), replace=False).tolist()
+        worst = out.setdefault(name, {"rows": 0})    # cases of one name (several posets) merge
+        done = worst.pop("rows")
+        for r in rows:
+            for dk, e in oracle_row_errors(p, outs, [r]).items():
+                w = worst.setdefault(dk, {})
+                for key, v in e.items():
+                    if isinstance(v, bool):
+                        w[key] = w.get(key, False) or v
+                    elif v is None or (key in w and w[key] is None):
+                        w[key] = None
+                    else:
+                        w[key] = max(w.get(key, 0.0), v)
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        worst["rows"] = done
+        out[name] = worst
+    out["note"] = ("largest componentwise error on sampled rows against the oracle (exact sums, correctly "
+                   "rounded): zeta |g - Zf| / Z|f|, Moebius residual (backward error) |Z m - g| / (Z|m| + |g|) "
+                   "of m = Moebius(g) for the GPU's own zeta output g; F32C values are (hi, lo) pairs taken "
+                   "exactly; inputs of the F32C and fp64 lines are the same fp32 values (C2, C3), or each "
+                   "dtype's own random values (C4). mobius_overflow: |M g| of rounded data exceeds the output "
+                   "type (it grows like 10^(0.23 U-levels) for any algorithm), so no residual exists")
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
 def _gen_one(spec_and_deg):
     (n, k, seed), deg = spec_and_deg
     p = pg.planted_chain_poset(n, k, seed, cross_deg=deg)
@@ -413,8 +490,44 @@ def batch_values(n, B, dtype_key, seed, torch):
     return torch.randint(-1000, 1001, (n, B), generator=gen, device="cuda", dtype=torch.int64)
 
 
-def run_batch_workload(mz, wl, posets, steps, warmup, torch, dtypes=("f32c", "f64"), graph=True):
-    """Builds one plan for all posets, autotunes it and times each dtype."""
+def time_batch_e2e(plan, x, steps, torch):
+    """The batched step through the public API from pinned host memory: H2D of the
+    inputs, zeta, Moebius of the result, D2H of both results, every step inside the
+    timed region (one buffer set, copies and compute in stream order)."""
+    h_in = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    h_in.copy_(x)
+    h_g = torch.empty_like(h_in, pin_memory=True)
+    h_f = torch.empty_like(h_in, pin_memory=True)
+    d_in = torch.empty_like(x)
+    g = torch.empty_like(x)
+    y = torch.empty_like(x)
+
+    def step():
+        d_in.copy_(h_in, non_blocking=True)
+        plan.zeta(d_in, out=g)
+        plan.mobius(g, out=y)
+        h_g.copy_(g, non_blocking=True)
+        h_f.copy_(y, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    e1.synchronize()
+    plan.check()
+    nbytes = x.numel() * x.element_size()
+    return e0.elapsed_time(e1), nbytes, 2 * nbytes
+
+
+def run_batch_workload(mz, wl, posets, steps, warmup, torch, dtypes=("f32c", "f64"), graph=True, e2e_steps=0,
+                       samples=None):
+    """Builds one plan for all posets, autotunes it and times each dtype (CUDA graph
+    replay); with e2e_steps also the end-to-end step from pinned host memory. samples:
+    a list of (poset index, column) whose inputs and outputs are copied to the host
+    (key "_samples", for the accuracy check of the CPU-baseline leg)."""
     from paper_2211_13706_gb300 import autotune
     w = BATCH_WORKLOADS[wl]
     t0 = time.perf_counter()
@@ -422,43 +535,107 @@ def run_batch_workload(mz, wl, posets, steps, warmup, torch, dtypes=("f32c", "f6
     build_s = time.perf_counter() - t0
     info = plan.info
     out = {"workload": w["desc"], "posets": info["components"], "n_total": info["n"], "k_total": info["k"],
-           "nnz": info["nnz"], "max_ulevels": info["ulevels"], "batch": w["batch"], "host_build_s": round(build_s, 1)}
+           "nnz": info["nnz"], "max_ulevels": info["ulevels"], "wave_rows": info["wave_rows"], "batch": w["batch"],
+           "host_build_s": round(build_s, 1)}
     peak, peak_kind = load_peaks()
     n, k, B, nnz = info["n"], info["k"], w["batch"], info["nnz"]
+    wave = (info["wave_rows"], info["wave_entries"])
+    offs = np.cumsum([0] + [int(q[0]) for q in posets])
+    kept = {}
     for dk in dtypes:
         x = batch_values(n, B, dk, 11, torch)
-        tuned = autotune.tune(plan, x)
+        tuned = autotune.tune(plan, x, reps=1)
         tot, used_graph = time_batch(mz, plan, x, steps, warmup, torch, graph)
         units = 2 * n * B * steps
         out[dk] = {"value": round(units / (tot / 1e3), 1), "unit": UNIT, "ms_per_step": round(tot / steps, 3),
                    "steps": steps, "cuda_graph": used_graph, "tuning": tuned}
         # per-kernel times of the same step, launched directly (inputs exceed L2: no flush)
-        kt, _, _, _, _, _ = time_transforms(mz, plan, x, 3, 1, torch, torch.empty(1, device="cuda"))
+        kt, _, _, _, g, y = time_transforms(mz, plan, x, 3, 1, torch, torch.empty(1, device="cuda"))
         out[dk]["kernels"] = {name: {"mean_ms": round(v, 4), "share": round(v / sum(kt.values()), 4),
-                                     "alg_GBps": round(algorithmic_bytes(name, n, k, B, nnz) / (v / 1e3) / 1e9, 1)}
+                                     "alg_GBps": round(algorithmic_bytes(name, n, k, B, nnz, wave) / (v / 1e3) / 1e9, 1)}
                               for name, v in kt.items()}
         dom = max(kt, key=kt.get)
-        alg = algorithmic_bytes(dom, n, k, B, nnz)
+        alg = algorithmic_bytes(dom, n, k, B, nnz, wave)
         achieved = alg / (kt[dom] / 1e3) / 1e9
         out[dk]["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                               "traffic": None, "algorithmic_bytes": alg}
-        # the gather's arithmetic roof: one add per gathered term and function
+                               "traffic": None, "algorithmic_bytes": alg, "mean_launch_ms": round(kt[dom], 4)}
+        # the gathers' arithmetic roof: one add per gathered term and function (zeta gather:
+        # nnz(N) terms; leaf gather: the same tiles)
         terms = nnz * B
-        t_g = kt["niv_gather"] / 1e3
-        if dk == "f32c":     # Sum2 step: TwoSum (6 fp32 adds) + 2 adds per term
-            ops, peak_ops = 8 * terms, torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2.07e9
-            out[dk]["gather_alu"] = {"fp32_ops": ops, "achieved_Tops": round(ops / t_g / 1e12, 2),
-                                     "peak_Tops": round(peak_ops / 1e12, 2), "frac": round(ops / t_g / peak_ops, 4),
-                                     "note": "peak = SMs x 128 fp32 lanes x 2.07 GHz (one add per lane per clock)"}
-        elif dk == "f64":
-            out[dk]["gather_alu"] = {"fp64_adds": terms, "achieved_Tadds": round(terms / t_g / 1e12, 3),
-                                     "peak_Tadds": FP64_ADDS_PER_S / 1e12,
-                                     "frac": round(terms / t_g / FP64_ADDS_PER_S, 4)}
+        alu = {}
+        for kname in ("niv_gather", "mob_leaf"):
+            t_g = kt[kname] / 1e3
+            if dk == "f32c":     # Sum2 step: TwoSum (6 fp32 adds) + 2 adds per term
+                ops, peak_ops = 8 * terms, torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2.07e9
+                alu[kname] = {"fp32_ops": ops, "achieved_Tops": round(ops / t_g / 1e12, 2),
+                              "peak_Tops": round(peak_ops / 1e12, 2), "frac": round(ops / t_g / peak_ops, 4),
+                              "note": "peak = SMs x 128 fp32 lanes x 2.07 GHz (one add per lane per clock)"}
+            elif dk == "f64":
+                alu[kname] = {"fp64_adds": terms, "achieved_Tadds": round(terms / t_g / 1e12, 3),
+                              "peak_Tadds": FP64_ADDS_PER_S / 1e12, "frac": round(terms / t_g / FP64_ADDS_PER_S, 4)}
+        out[dk]["gather_alu"] = alu.get("niv_gather")
+        out[dk]["leaf_alu"] = alu.get("mob_leaf")
+        if samples:
+            for (pi, b) in samples:
+                sl = slice(int(offs[pi]), int(offs[pi + 1]))
+                if dk == "f32c":
+                    pick = lambda t: (t[0, sl, b].cpu().numpy(), t[1, sl, b].cpu().numpy())
+                else:
+                    pick = lambda t: t[sl, b].cpu().numpy()
+                kept.setdefault((pi, b), {})[dk] = (pick(x), pick(g), pick(y))
+        del g, y
+        if e2e_steps:
+            torch.cuda.empty_cache()
+            ms, h2d, d2h = time_batch_e2e(plan, x, e2e_steps, torch)
+            out[dk]["e2e"] = {"value": round(2 * n * B * e2e_steps / (ms / 1e3), 1), "unit": UNIT,
+                              "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                              "ms_per_step": round(ms / e2e_steps, 3),
+                              "copies": "pinned host memory, H2D of f, D2H of zeta(f) and Moebius(zeta(f)), "
+                                        "in stream order"}
         del x
         torch.cuda.empty_cache()
     plan.close()
+    if samples:
+        out["_samples"] = kept
     return out
+
+
+def time_c3(mz, torch, flush, steps: int = 10):
+    """The precision workload: n = 2^22, k = 128 chains, cross out-degree 2, B = 1, f fp32
+    uniform [-1, 1] and log-normal (sigma = 3, random signs); compensated F32C and plain
+    fp64 on the same values, plan built on the device and its launch shapes autotuned.
+    Returns the timings and the poset with host copies of inputs and outputs (for the
+    accuracy check of the CPU-baseline leg)."""
+    from paper_2211_13706_gb300 import autotune
+    p = make_poset("c3", 1)
+    t0 = time.perf_counter()
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, device_build=True)
+    build_s = time.perf_counter() - t0
+    info = plan.info
+    res = {"workload": WORKLOADS["c3"]["desc"] + "; B=1", "n": p.n, "k": info["k"], "nnz": info["nnz"],
+           "ulevels": info["ulevels"], "wave_rows": info["wave_rows"], "device_build_s": round(build_s, 2)}
+    kept = {}
+    for kind in ("u", "ln"):
+        f32 = pg.function_values(p.n, 1, "f32" + kind, 13)[:, 0]
+        res[kind] = {}
+        for dk in ("f32c", "f64"):
+            x = to_dev(f32 if dk == "f32c" else f32.astype(np.float64), dk, torch)
+            tuned = autotune.tune(plan, x, reps=2)
+            kt, total, _, _, g, y = time_transforms(mz, plan, x, steps, 3, torch, flush)
+            zms = kt["chain_scan"] + kt["niv_gather"]
+            res[kind][dk] = {"value": round(2 * p.n * steps / (total / 1e3), 1), "unit": UNIT,
+                             "zeta_ms": round(zms, 4), "mobius_ms": round(total / steps - zms, 4),
+                             "kernels_ms": {a: round(b, 4) for a, b in kt.items()}, "tuning": tuned}
+            if dk == "f32c":
+                host = lambda t: (t[0].cpu().numpy(), t[1].cpu().numpy())
+                kept.setdefault(kind, {})[dk] = ((f32, np.zeros_like(f32)), host(g), host(y))
+            else:
+                kept.setdefault(kind, {})[dk] = (f32.astype(np.float64), g.cpu().numpy(), y.cpu().numpy())
+            del x, g, y
+    plan.close()
+    torch.cuda.empty_cache()
+    return res, p, kept
 
 
 def time_seeds(mz, torch, wl: str, dtype_key: str, flush, seeds=(1, 2, 3, 4, 5), steps: int = 20):
@@ -595,7 +772,7 @@ def device_arm(args):
     if args.workload in BATCH_WORKLOADS:
         return batch_arm(args, gen_batch_posets(args.workload, rank_seed(rank)))
     if not args.no_variants:
-        batch_posets = gen_batch_posets("c4s", rank_seed(rank))
+        batch_posets = gen_batch_posets("c4", rank_seed(rank))
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -612,6 +789,9 @@ def device_arm(args):
     f_np = pg.function_values(p.n, 1, kind, 2 + rank)[:, 0]
     x = to_dev(f_np, args.dtype, torch)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    # launch shapes picked by the autotuner for this plan and input (results do not depend on them)
+    from paper_2211_13706_gb300 import autotune
+    tuned = autotune.tune(plan, x)
 
     sampler = ClockSampler(local)
     if dist:
@@ -629,6 +809,23 @@ def device_arm(args):
     if args.dtype == "i64":
         assert torch.equal(y, x), "Moebius(zeta(f)) != f"
 
+    # the accuracy inputs: one fp32-valued function through the F32C and the fp64 path (the
+    # same values), outputs kept on the host for the CPU-baseline leg's oracle rows
+    f32 = pg.function_values(p.n, 1, "f32u", 20 + rank)[:, 0]
+    acc_c2 = {}
+    for dk in ("f32c", "f64"):
+        xa = to_dev(f32 if dk == "f32c" else f32.astype(np.float64), dk, torch)
+        mz.mz_plan_tune(plan.handle, **tuned)
+        ga = plan.zeta(xa)
+        ma = plan.mobius(ga)
+        plan.check()
+        if dk == "f32c":
+            host = lambda t: (t[0].cpu().numpy(), t[1].cpu().numpy())
+            acc_c2[dk] = ((f32, np.zeros_like(f32)), host(ga), host(ma))
+        else:
+            acc_c2[dk] = (f32.astype(np.float64), ga.cpu().numpy(), ma.cpu().numpy())
+        del xa, ga, ma
+
     e2e_ms, h2d, d2h = time_e2e(mz, plan, f_np, args.dtype, max(5, min(args.steps, 50)), torch)
     e2e_steps = max(5, min(args.steps, 50))
     e2e_val = 2 * n * B * e2e_steps * world / (e2e_ms / 1e3)
@@ -640,14 +837,15 @@ def device_arm(args):
 
     peak, peak_kind = load_peaks()
     dom = max(kt, key=kt.get)
-    alg = algorithmic_bytes(dom, n, k, B, info["nnz"])
+    wave = (info["wave_rows"], info["wave_entries"])
+    alg = algorithmic_bytes(dom, n, k, B, info["nnz"], wave)
     achieved = alg / (kt[dom] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": peak_kind,
             "traffic": load_traffic(dom, args.workload, args.dtype), "algorithmic_bytes": alg,
             "mean_launch_ms": round(kt[dom], 5)}
     kernels = {name: {"mean_ms": round(v, 5), "share": round(v / sum(kt.values()), 4),
-                      "alg_GBps": round(algorithmic_bytes(name, n, k, B, info["nnz"]) / (v / 1e3) / 1e9, 1)}
+                      "alg_GBps": round(algorithmic_bytes(name, n, k, B, info["nnz"], wave) / (v / 1e3) / 1e9, 1)}
                for name, v in kt.items()}
     # The gather's other roof: one add per gathered term (nnz(N) per launch). In fp64 it is
     # bound by the FP64 pipe: nominal 1.25 TFLOP/s = 0.625e12 adds/s on GB300.
@@ -664,6 +862,7 @@ def device_arm(args):
                "frac": round(lat_ms / kt["mob_wave"], 4)}
 
     variants = {}
+    c3 = p3 = acc_c3 = None
     if not args.no_variants:
         for vd in ("i64", "f32c"):
             if vd == args.dtype:
@@ -686,23 +885,44 @@ def device_arm(args):
             pd.close()
         pa = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
         kta, tot, _, _, _, _ = time_transforms(mz, pa, x, 3, 1, torch, flush, anti=True)
-        variants["differentiation_c5"] = time_differentiation(mz, torch)
-        variants["seeds_1_to_5"] = time_seeds(mz, torch, args.workload, args.dtype, flush)
-        variants["paper_er_n2^20_deg4"] = time_single(mz, torch, "er1m4", args.dtype)
-        variants["paper_er_n2^20_deg6"] = time_single(mz, torch, "er1m6", args.dtype)
-        if batch_posets is not None:
-            variants["batched_c4s"] = run_batch_workload(mz, "c4s", batch_posets, args.variant_steps // 5 or 3,
-                                                         3, torch)
         variants["mobius_antichain_schedule_" + args.dtype] = {
             "mobius_ms": round(kta["mob_init"] + kta["mob_wave"], 4), "levels": pa.info["levels"],
             "note": "Alg. 5/6 schedule (antichain levels) instead of U's dependency levels"}
         pa.close()
+        variants["differentiation_c5"] = time_differentiation(mz, torch)
+        variants["seeds_1_to_5"] = time_seeds(mz, torch, args.workload, args.dtype, flush)
+        variants["paper_er_n2^20_deg4"] = time_single(mz, torch, "er1m4", args.dtype)
+        variants["paper_er_n2^20_deg6"] = time_single(mz, torch, "er1m6", args.dtype)
+        c3, p3, acc_c3 = time_c3(mz, torch, flush)
+    del flush
+    torch.cuda.empty_cache()
+    c4 = None
+    c4_samples = [(int(q), 31 if i == 0 else 0) for i, q in
+                  enumerate(np.random.default_rng(5).choice(len(batch_posets), 6, replace=False))] \
+        if batch_posets is not None else []
+    if batch_posets is not None:
+        plan.close()
+        c4 = run_batch_workload(mz, "c4", batch_posets, max(3, args.steps // 4), 3, torch, e2e_steps=3,
+                                samples=c4_samples)
 
-    cpu = cpu_fast = None
+    cpu = cpu_fast = accuracy = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(p, f_np, args.cpu_budget, 64)
+        if args.dtype in ("f64", "i64") and not plan.handle:
+            plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, host_only=True)
         if args.dtype in ("f64", "i64"):
             cpu_fast = cpu_paper_method(mz, plan, f_np, args.dtype, g.cpu().numpy())
+        cases = [("c2", p, acc_c2, 6)]
+        if not args.no_variants:
+            cases += [("c3_uniform", p3, acc_c3["u"], 2), ("c3_lognormal", p3, acc_c3["ln"], 2)]
+        if c4 is not None:
+            for (pi, b), outs in c4.pop("_samples").items():
+                n_, s_, d_, c_ = batch_posets[pi]
+                cases.append(("c4", pg.Poset(n=n_, src=s_, dst=d_, chain_id=c_), outs, 3))
+        try:
+            accuracy = accuracy_leg(cases, args.accuracy_budget)
+        except Exception as exc:          # keep the measured line; say what failed
+            accuracy = {"error": f"{type(exc).__name__}: {exc}"}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -724,6 +944,10 @@ def device_arm(args):
                 "copies": "pinned host memory; double-buffered: step i+1's H2D and step i's D2H overlap compute"},
         "gpu_launches": launches,
         "clocks": clocks,
+        "tuning": tuned,
+        "accuracy": accuracy,
+        "c3_precision": c3,
+        "c4_batched": c4,
         "variants": variants,
     }
     print(json.dumps(line))
@@ -765,7 +989,7 @@ def batch_arm(args, posets):
                        "cuda_graph": main["cuda_graph"], "tuning": main["tuning"],
                        "parallelism": f"replicas x{world}"},
             "roofline": main["roofline"], "kernels": main["kernels"], "gather_alu": main.get("gather_alu"),
-            "fp64_plain": res.get("f64"), "clocks": clocks, "gpu_launches": 5 * main["steps"]}
+            "fp64_plain": res.get("f64"), "clocks": clocks, "gpu_launches": 6 * main["steps"]}
     print(json.dumps(line))
 
 
@@ -823,6 +1047,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--accuracy-budget", type=float, default=90.0,
+                    help="seconds of oracle rows for the accuracy figures (CPU-baseline leg)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)          # at least 3 untimed warm-up steps
     if args.impl == "reference":

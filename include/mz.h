@@ -31,8 +31,7 @@
  *    double-word fp32 pairs stored as two planes: the hi plane ([n][batch]
  *    floats) followed directly by the lo plane; the value is hi + lo.
  *    Inputs with plain fp32 data pass a zero lo plane.
- *  - int64 arithmetic wraps on overflow; keeping every partial sum inside
- *    (-2^63, 2^63) is the caller's responsibility.
+ *  - int64 arithmetic wraps on overflow: results are exact modulo 2^64.
  *  - f, g and ws are device pointers the caller owns. Input and output must
  *    not overlap. Calls on one workspace must not overlap in time.
  *  - Errors found on the host are returned directly and nothing is launched.
@@ -87,7 +86,7 @@ typedef struct {
     int32_t host_only;        /* nonzero: build host structures only (no device use at all) */
     int32_t mobius_schedule;  /* an mz_schedule value */
     int32_t mobius_blocks_per_sm; /* resident 128-thread blocks per SM of the Moebius forward
-                                     substitution (one thread per row); 0 = default (2) */
+                                     substitution, per lane of a row; 0 = default (2) */
     int32_t mobius_pace_ns;   /* Moebius forward substitution: before polling for a row that is
                                  d levels above the row it just finished, a thread sleeps about
                                  (d - 2) * pace ns, so rows far from the frontier do not load L2
@@ -132,6 +131,11 @@ typedef struct {
     int64_t device_bytes;  /* device memory held by the plan (dual included) */
     int32_t components;    /* posets in the plan (1 for mz_build) */
     int32_t sparse;        /* how many of them keep a sparse niv map */
+    int64_t wave_rows;     /* rows of the Moebius forward substitution (0 for a host-only plan):
+                              with MZ_SCHED_ULEVEL only the elements some row of another chain
+                              reads (niv_j(x) = y for an x not on y's chain); the others are
+                              computed afterwards by a gather. All n with MZ_SCHED_ANTICHAIN */
+    int64_t wave_entries;  /* their finite niv entries on other chains */
 } mz_plan_info_t;
 /* For a plan of several posets (mz_build_batch) n, k, nnz and edges are totals over
    them and levels, ulevels, levels_T, ulevels_T and max_chain are maxima. */
@@ -212,9 +216,16 @@ mz_status mz_zeta(const mz_plan *plan, mz_dtype dtype, const void *f, void *g, i
 
 /*
  * mz_mobius - f = M g (Thm. 1 right) by the fast Moebius transform of Sec. 3:
- * forward substitution y'(x) = g(x) - sum_{j != id(x)} y'(niv_j(x)) in a
- * persistent kernel that follows the plan's schedule, then f(x) = y'(x) -
- * y'(next(x)) (V^-1). Arguments as for mz_zeta (g in, f out).
+ * forward substitution y'(x) = g(x) - sum_{j != id(x)} y'(niv_j(x)) (Alg. 4), then
+ * f(x) = y'(x) - y'(next(x)) (V^-1). Arguments as for mz_zeta (g in, f out).
+ * With MZ_SCHED_ULEVEL a persistent kernel substitutes, in the order of U's
+ * dependency levels, only the rows some row of another chain reads; the remaining
+ * rows (on the planted and random posets most of them) read only finished values
+ * and are computed next by a gather over the zeta map, then V^-1 runs (4 launches).
+ * MZ_SCHED_ANTICHAIN substitutes every row by antichain levels (Alg. 5) and writes
+ * f directly (2 launches). MZ_F32C keeps y' in fp64 in the forward substitution; the
+ * gather and V^-1 then run in compensated fp32 on double-word copies of y'. int64
+ * results are exact modulo 2^64 for every input.
  */
 mz_status mz_mobius(const mz_plan *plan, mz_dtype dtype, const void *g, void *f, int32_t batch,
                     void *ws, size_t ws_bytes, mz_stream stream);
@@ -269,9 +280,14 @@ mz_status mz_check(const mz_plan *plan, mz_stream stream);
    value). An autotuner times transforms under candidate shapes and keeps the best. */
 typedef struct {
     int32_t mobius_blocks_per_sm; /* as mz_build_opts::mobius_blocks_per_sm (default 2) */
-    int32_t mobius_pace_ns;       /* as mz_build_opts::mobius_pace_ns (default 500; < 0 = none) */
+    int32_t mobius_pace_ns;       /* as mz_build_opts::mobius_pace_ns (default 600; < 0 = none) */
     int32_t gather_blocks_per_sm; /* resident 256-thread blocks per SM of the zeta gather (default 32) */
-    int32_t reserved;
+    int32_t mobius_lanes;         /* forward substitution of one function (batch 1): lanes sharing one
+                                     row, a power of two up to 32 (default 32, or 1 when no row has
+                                     more than 16 entries on other chains). The row's entries are
+                                     dealt to the lanes 16 at a time, each lane polls its own, and the
+                                     lane holding the last 16 adds the lanes' sums and publishes the
+                                     row; 0 keeps the current value */
 } mz_tuning;
 
 /* Sets the plan's launch shapes (results are unaffected); fills *current if non-NULL. */

@@ -16,8 +16,9 @@ from . import mz_plan_tune
 
 CANDIDATES = {
     "mobius_blocks_per_sm": (1, 2, 3, 4),
-    "mobius_pace_ns": (300, 500, 800, 1500),
+    "mobius_pace_ns": (300, 600, 1000, 1600),
     "gather_blocks_per_sm": (8, 16, 32),
+    "mobius_lanes": (1, 32),               # one function per row only
 }
 _CACHE: dict = {}
 
@@ -79,6 +80,14 @@ def tune(plan, x, reps: int = 3) -> dict:
         t = _time(lambda: plan.zeta(x, out=g), reps)
         if best_g is None or t < best_g[0]:
             best_g = (t, gb)
+    best_l = None
+    if batch == 1:    # lanes per row first, at the current blocks and pacing
+        for lanes in CANDIDATES["mobius_lanes"]:
+            mz_plan_tune(plan.handle, mobius_lanes=lanes)
+            t = _time(lambda: plan.mobius(g, out=y), reps)
+            if best_l is None or t < best_l[0]:
+                best_l = (t, lanes)
+        mz_plan_tune(plan.handle, mobius_lanes=best_l[1])
     best_m = None
     for bps in CANDIDATES["mobius_blocks_per_sm"]:
         for pace in CANDIDATES["mobius_pace_ns"]:
@@ -88,6 +97,8 @@ def tune(plan, x, reps: int = 3) -> dict:
                 best_m = (t, bps, pace)
     plan.check()
     choice = {"gather_blocks_per_sm": best_g[1], "mobius_blocks_per_sm": best_m[1], "mobius_pace_ns": best_m[2]}
+    if best_l is not None:
+        choice["mobius_lanes"] = best_l[1]
     mz_plan_tune(plan.handle, **choice)
     _CACHE[key] = choice
     _save_file()

@@ -130,6 +130,31 @@ static mz_status upload_side(mz_plan *p, int side) {
             }
         if ((st = upload(p, &D.slot_node, sn.data(), sn.size()))) return st;
     }
+    // U-level schedule: the slots some row of another chain reads (an entry of another
+    // chain in its niv row). Only their rows go through the forward substitution; every
+    // other row is read by no row and is computed afterwards by the leaf gather.
+    const bool anti = (p->schedule == MZ_SCHED_ANTICHAIN);
+    std::vector<uint8_t> ref;
+    if (!anti) {
+        std::unique_ptr<std::atomic<uint8_t>[]> refa(new std::atomic<uint8_t>[(size_t)D.nslots]());
+        parallel_for((int64_t)C == 1 ? Hs[0].n : (int64_t)C, [&](int64_t lo, int64_t hi) {
+            const bool rows = (C == 1);
+            for (int64_t u = lo; u < hi; ++u) {
+                const size_t c = rows ? 0 : (size_t)u;
+                const HostSide &H = Hs[c];
+                const int64_t so = p->slot_off[c];
+                for (int64_t r = rows ? u : 0, r1 = rows ? u + 1 : H.n; r < r1; ++r) {
+                    const int32_t cx = H.chain_id[H.row_node[r]];
+                    H.for_row(r, [&](int32_t ch, int32_t slot) {
+                        if (ch != cx) refa[(size_t)(so + slot)].store(1, std::memory_order_relaxed);
+                    });
+                }
+            }
+        });
+        ref.resize((size_t)D.nslots);
+        for (size_t q = 0; q < ref.size(); ++q) ref[q] = refa[q].load(std::memory_order_relaxed);
+        if ((st = upload(p, &D.slot_ref, ref.data(), ref.size()))) return st;
+    }
     {   // tiles of 32 rows per component, column-major inside a tile
         std::vector<int64_t> toff;
         std::vector<int32_t> tk;
@@ -155,7 +180,8 @@ static mz_status upload_side(mz_plan *p, int side) {
             }
         }
         D.ntiles = (int64_t)toff.size();
-        std::vector<int32_t> tiled, rn((size_t)D.ntiles * kTileRows, -1);
+        std::vector<int32_t> tiled, rn((size_t)D.ntiles * kTileRows, -1), rl;
+        if (!anti) rl.assign((size_t)D.ntiles * kTileRows, -1);
         try {
             tiled.assign(total, 0);   // padding rows read slot 0, a zero slot
         } catch (...) {
@@ -185,30 +211,44 @@ static mz_status upload_side(mz_plan *p, int side) {
                         for (int64_t q = 0; q < k; ++q) dst[q * kTileRows] = row[q] + so;
                     }
                     rn[(size_t)t * kTileRows + lane] = (int32_t)(H.row_node[r] + p->node_off[c]);
+                    if (!anti) {
+                        const int32_t gs = H.node_slot[H.row_node[r]] + so;
+                        rl[(size_t)t * kTileRows + lane] = ref[(size_t)gs] ? -1 : gs;
+                    }
                 }
             }
         });
         if ((st = upload(p, &D.Nt, tiled.data(), tiled.size()))) return st;
+        if (!anti && (st = upload(p, &D.row_leaf, rl.data(), rl.size()))) return st;
         if ((st = upload(p, &D.tile_off, toff.data(), toff.size()))) return st;
         if ((st = upload(p, &D.tile_k, tk.data(), tk.size()))) return st;
         if ((st = upload(p, &D.row_node, rn.data(), rn.size()))) return st;
     }
-    {   // Moebius rows: all components in one order, by level, then component, then row
-        const bool anti = (p->schedule == MZ_SCHED_ANTICHAIN);
+    {   // Moebius rows: all components in one order, by level, then component, then row;
+        // the U-level schedule keeps only the referenced rows
         int32_t maxlvl = 0;
         for (const HostSide &H : Hs) maxlvl = std::max(maxlvl, anti ? H.nlevels : H.nulevels);
+        auto in_schedule = [&](size_t c, int64_t r) {
+            return anti || ref[(size_t)(Hs[c].node_slot[Hs[c].row_node[r]] + p->slot_off[c])] != 0;
+        };
         std::vector<int64_t> cnt((size_t)maxlvl + 2, 0);
-        for (const HostSide &H : Hs)
-            for (int64_t r = 0; r < H.n; ++r) cnt[(anti ? H.level : H.ulevel)[H.row_node[r]] + 1]++;
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
+            for (int64_t r = 0; r < H.n; ++r)
+                if (in_schedule(c, r)) cnt[(anti ? H.level : H.ulevel)[H.row_node[r]] + 1]++;
+        }
         for (size_t l = 1; l < cnt.size(); ++l) cnt[l] += cnt[l - 1];
-        std::vector<std::pair<int32_t, int32_t>> order((size_t)D.n);   // (component, row)
+        D.nmob = cnt.back();
+        std::vector<std::pair<int32_t, int32_t>> order((size_t)D.nmob);   // (component, row)
         for (size_t c = 0; c < C; ++c) {
             const HostSide &H = Hs[c];
             const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
-            for (int64_t r = 0; r < H.n; ++r) order[(size_t)cnt[lvl[H.row_node[r]]]++] = {(int32_t)c, (int32_t)r};
+            for (int64_t r = 0; r < H.n; ++r)
+                if (in_schedule(c, r)) order[(size_t)cnt[lvl[H.row_node[r]]]++] = {(int32_t)c, (int32_t)r};
         }
-        std::vector<int64_t> moff((size_t)D.n);
-        std::vector<int32_t> mkp((size_t)D.n), mnode((size_t)D.n), mslot((size_t)D.n), mlevel((size_t)D.n);
+        std::vector<int64_t> moff((size_t)D.nmob);
+        std::vector<int32_t> mkp((size_t)D.nmob), mnode((size_t)D.nmob), mslot((size_t)D.nmob), mlevel((size_t)D.nmob);
+        std::vector<int64_t> ment((size_t)D.nmob);
         // A row holds the finite entries of the other chains (the own chain and the
         // infinite entries add nothing), padded in front to a multiple of 16, at least 16.
         parallel_for((int64_t)order.size(), [&](int64_t lo, int64_t hi) {
@@ -216,12 +256,17 @@ static mz_status upload_side(mz_plan *p, int side) {
                 const HostSide &H = Hs[order[i].first];
                 const int64_t cnt = H.row_count(order[i].second) - 1;   // minus the own chain
                 mkp[i] = (int32_t)std::max<int64_t>(16, (cnt + 15) / 16 * 16);
+                ment[i] = cnt;
             }
         });
         size_t total = 0;
+        D.nmob_entries = 0;
+        D.mob_kp_max = 0;
         for (size_t i = 0; i < order.size(); ++i) {
             moff[i] = (int64_t)total;
             total += (size_t)mkp[i];
+            D.nmob_entries += ment[i];
+            D.mob_kp_max = std::max(D.mob_kp_max, mkp[i]);
         }
         std::vector<int32_t> Nm;
         try {
@@ -514,6 +559,7 @@ static mz_status upload_side_device(mz_plan *p, int side) {
     for (int64_t x = 0; x < n; ++x) H.ulevel[x] = uslot[H.node_slot[x]];
     H.nulevels = *std::max_element(H.ulevel.begin(), H.ulevel.end()) + 1;
     // ---- tiles of 32 rows for the gather
+    std::vector<int32_t> rn_host;   // node of each tile row (-1: padding)
     {
         D.ntiles = (n + kTileRows - 1) / kTileRows;
         std::vector<int64_t> toff((size_t)D.ntiles);
@@ -546,24 +592,59 @@ static mz_status upload_side_device(mz_plan *p, int side) {
                                                  D.tile_k, D.Nt, p->num_sms, 0)
                      : launch_build_tiles(d_N, n, (int32_t)k, D.Nt, p->num_sms, 0);
         if (e != cudaSuccess) return cuda_fail(e, "tile build launch");
+        rn_host.swap(rn);
+    }
+    // ---- U-level schedule: the slots another chain's row reads (marked from the tiles);
+    // only their rows go through the forward substitution, the others through the leaf gather
+    const bool anti = (p->schedule == MZ_SCHED_ANTICHAIN);
+    std::vector<uint8_t> ref;
+    if (!anti) {
+        D.slot_ref = (uint8_t *)plan_alloc(p, (size_t)nslots);
+        if (!D.slot_ref) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        if ((e = cudaMemset(D.slot_ref, 0, (size_t)nslots)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+        if ((e = launch_mark_referenced(D.Nt, D.tile_off, D.tile_k, D.row_node, D.ntiles, d_node_slot, D.slot_node,
+                                        D.slot_ref, p->num_sms, 0)) != cudaSuccess)
+            return cuda_fail(e, "reference marking launch");
+        ref.resize((size_t)nslots);
+        if ((e = cudaMemcpy(ref.data(), D.slot_ref, (size_t)nslots, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy");
+        std::vector<int32_t> rl(rn_host.size(), -1);
+        for (size_t q = 0; q < rn_host.size(); ++q)
+            if (rn_host[q] >= 0) {
+                const int32_t gs = H.node_slot[rn_host[q]];
+                rl[q] = ref[(size_t)gs] ? -1 : gs;
+            }
+        if ((st = upload(p, &D.row_leaf, rl.data(), rl.size()))) return st;
     }
     // ---- Moebius rows, by level of the schedule and then by row
     {
-        const bool anti = (p->schedule == MZ_SCHED_ANTICHAIN);
         const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
         const int32_t maxlvl = anti ? H.nlevels : H.nulevels;
+        auto in_schedule = [&](int64_t r) { return anti || ref[(size_t)H.node_slot[H.row_node[r]]] != 0; };
         std::vector<int64_t> cnt((size_t)maxlvl + 2, 0);
-        for (int64_t r = 0; r < n; ++r) cnt[lvl[H.row_node[r]] + 1]++;
+        for (int64_t r = 0; r < n; ++r)
+            if (in_schedule(r)) cnt[lvl[H.row_node[r]] + 1]++;
         for (size_t l = 1; l < cnt.size(); ++l) cnt[l] += cnt[l - 1];
-        std::vector<int32_t> mrow((size_t)n), mkp((size_t)n), mnode((size_t)n), mslot((size_t)n), mlevel((size_t)n);
-        std::vector<int64_t> moff((size_t)n);
-        for (int64_t r = 0; r < n; ++r) mrow[(size_t)cnt[lvl[H.row_node[r]]]++] = (int32_t)r;
+        const int64_t nm = cnt.back();
+        D.nmob = nm;
+        std::vector<int32_t> mrow((size_t)nm), mkp((size_t)nm), mnode((size_t)nm), mslot((size_t)nm),
+            mlevel((size_t)nm);
+        std::vector<int64_t> moff((size_t)nm);
+        for (int64_t r = 0; r < n; ++r)
+            if (in_schedule(r)) mrow[(size_t)cnt[lvl[H.row_node[r]]]++] = (int32_t)r;
         int64_t total = 0;
-        for (int64_t i = 0; i < n; ++i) {
+        D.nmob_entries = 0;
+        D.mob_kp_max = 0;
+        for (int64_t i = 0; i < nm; ++i) {
             const int32_t r = mrow[i], x = H.row_node[r];
             mkp[i] = std::max<int32_t>(16, (rowcnt[r] - 1 + 15) / 16 * 16);
+            D.mob_kp_max = std::max(D.mob_kp_max, mkp[i]);
             moff[i] = total;
             total += mkp[i];
+            D.nmob_entries += rowcnt[r] - 1;
             mnode[i] = x;
             mslot[i] = H.node_slot[x];
             mlevel[i] = lvl[x];
@@ -599,7 +680,7 @@ static mz_status upload_side_device(mz_plan *p, int side) {
             b.mkp = D.mob_kp;
             b.mslot = D.mob_slot;
             b.key_slot = key_slot;
-            b.n = n;
+            b.n = nm;
             b.Nm = D.Nm;
             e = launch_build_mob_rows(b, p->num_sms, 0);
         } else {
@@ -612,7 +693,7 @@ static mz_status upload_side_device(mz_plan *p, int side) {
             b.mkp = D.mob_kp;
             b.mslot = D.mob_slot;
             b.key_slot = key_slot;
-            b.n = n;
+            b.n = nm;
             b.Nm = D.Nm;
             e = launch_build_mob_rows_sparse(b, p->num_sms, 0);
         }
@@ -627,21 +708,33 @@ static mz_status upload_side_device(mz_plan *p, int side) {
 // ---------------------------------------------------------------- workspace
 struct WsLayout {
     ScanShape sh;
-    size_t counters = 0, flags = 0, agg = 0, inc = 0, P = 0, memset_bytes = 0, total = 0;
+    size_t counters = 0, flags = 0, agg = 0, inc = 0, P = 0, esc = 0, Q = 0, memset_bytes = 0, total = 0;
 };
 
-static WsLayout ws_layout(const mz_plan *p, int32_t B) {
+// Workspace: the scan's look-back state, the prefix array y' ([nslots][B] 8-byte words),
+// and for the Moebius transform the escape flags of int64 words ([nslots][B] bytes) or
+// the double-word copies of y' for F32C ([nslots][B] float pairs).
+static WsLayout ws_layout(const mz_plan *p, int32_t B, int dtype) {
     WsLayout L;
     const int64_t nslots = p->slots_total();
     L.sh = scan_shape(nslots, B);
     const size_t tiles = (size_t)L.sh.groups * (size_t)L.sh.ntiles;
+    const size_t words = (size_t)nslots * (size_t)B;
     L.counters = 0;
     L.flags = align256(sizeof(uint32_t) * L.sh.groups);
     L.agg = L.flags + align256(sizeof(uint32_t) * tiles);
     L.memset_bytes = L.agg;
     L.inc = L.agg + align256(8 * tiles * L.sh.BW);
     L.P = L.inc + align256(8 * tiles * L.sh.BW);
-    L.total = L.P + align256((size_t)8 * (size_t)nslots * (size_t)B);
+    size_t end = L.P + align256(8 * words);
+    if (dtype == MZ_I64) {
+        L.esc = end;
+        end += align256(words);
+    } else if (dtype == MZ_F32C) {
+        L.Q = end;
+        end += align256(8 * words);
+    }
+    L.total = end;
     return L;
 }
 
@@ -672,7 +765,7 @@ static mz_status check_call(const mz_plan *p, int dtype, const void *in, const v
         set_last_error("batch must be >= 1");
         return MZ_ERR_INVALID_ARG;
     }
-    *L = ws_layout(p, B);
+    *L = ws_layout(p, B, dtype);
     if (ws_bytes < L->total || ((uintptr_t)ws & 255)) {
         set_last_error("workspace too small or not 256-byte aligned");
         return MZ_ERR_INVALID_ARG;
@@ -756,7 +849,6 @@ static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const vo
     ma.mob_slot = D.mob_slot;
     ma.mob_level = D.mob_level;
     ma.pace_ns = p->mob_pace_ns;
-    ma.n = D.n;
     ma.B = B;
     ma.g = g;
     ma.f = f;
@@ -765,6 +857,18 @@ static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const vo
     ma.status = p->d_status;
     ma.spin_limit = p->spin_limit;
     ma.withhold = p->withhold;
+    ma.n = D.nmob;
+    ma.esc = dtype == MZ_I64 ? (unsigned char *)ws + L.esc : nullptr;
+    ma.Q = dtype == MZ_F32C ? (float2 *)((char *)ws + L.Q) : nullptr;
+    ma.slot_ref = D.slot_ref;
+    ma.Nt = D.Nt;
+    ma.tile_off = D.tile_off;
+    ma.tile_k = D.tile_k;
+    ma.row_node = D.row_node;
+    ma.row_leaf = D.row_leaf;
+    ma.ntiles = D.ntiles;
+    ma.gather_blocks_per_sm = p->gather_blocks_per_sm;
+    ma.lanes = p->mob_lanes;
     int launches = 0;
     mark_event(0, (cudaStream_t)stream);
     cudaError_t e = launch_mobius(dtype, ma, D.slot_node, D.nslots, p->schedule == MZ_SCHED_ANTICHAIN, p->num_sms,
@@ -915,6 +1019,9 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
             plan_free_all(p.get());
             return st;
         }
+        // rows of one chunk (16 entries or fewer, as on the sparse random DAGs) leave nothing
+        // to share between lanes: one lane per row; longer rows: a warp per row
+        p->mob_lanes = p->dev[0].mob_kp_max <= 16 ? 1 : 32;
     }
     *out = p.release();
     return MZ_OK;
@@ -954,7 +1061,7 @@ mz_status mz_workspace_size(const mz_plan *plan, mz_dtype dtype, int32_t batch, 
         set_last_error("invalid argument");
         return MZ_ERR_INVALID_ARG;
     }
-    *bytes = ws_layout(plan, batch).total;   // primal and dual share the slot count
+    *bytes = ws_layout(plan, batch, dtype).total;   // primal and dual share the slot count
     return MZ_OK;
 }
 
@@ -1039,7 +1146,7 @@ mz_status mz_zeta_noalloc(const mz_plan *plan, mz_dtype dtype, const void *f, vo
         set_last_error("plan was built host-only");
         return MZ_ERR_NO_DEVICE;
     }
-    const size_t need = ws_layout(plan, batch).total;
+    const size_t need = ws_layout(plan, batch, dtype).total;
     if (need > MZ_NOALLOC_SCRATCH_BYTES) {
         set_last_error("mz_zeta_noalloc: this plan and batch need " + std::to_string(need) +
                        " bytes of scratch; the fixed scratch array holds " +
@@ -1104,19 +1211,22 @@ mz_status mz_plan_tune(mz_plan *plan, const mz_tuning *set, mz_tuning *current) 
     }
     if (set) {
         if (set->mobius_blocks_per_sm < 0 || set->mobius_blocks_per_sm > 64 || set->gather_blocks_per_sm < 0 ||
-            set->gather_blocks_per_sm > 256) {
+            set->gather_blocks_per_sm > 256 || set->mobius_lanes < 0 || set->mobius_lanes > 32 ||
+            (set->mobius_lanes & (set->mobius_lanes - 1)) != 0) {
             set_last_error("tuning value out of range");
             return MZ_ERR_INVALID_ARG;
         }
         if (set->mobius_blocks_per_sm) plan->mob_blocks_per_sm = set->mobius_blocks_per_sm;
         if (set->mobius_pace_ns) plan->mob_pace_ns = set->mobius_pace_ns < 0 ? 0 : set->mobius_pace_ns;
         if (set->gather_blocks_per_sm) plan->gather_blocks_per_sm = set->gather_blocks_per_sm;
+        if (set->mobius_lanes) plan->mob_lanes = set->mobius_lanes;
     }
     if (current) {
         std::memset(current, 0, sizeof(*current));
         current->mobius_blocks_per_sm = plan->mob_blocks_per_sm;
         current->mobius_pace_ns = plan->mob_pace_ns ? plan->mob_pace_ns : -1;
         current->gather_blocks_per_sm = plan->gather_blocks_per_sm;
+        current->mobius_lanes = plan->mob_lanes;
     }
     return MZ_OK;
 }
@@ -1142,6 +1252,10 @@ mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info) {
         info->ulevels_T = std::max(info->ulevels_T, H.nulevels);
     }
     info->device_bytes = plan->device_bytes;
+    if (!plan->host_only) {
+        info->wave_rows = plan->dev[0].nmob;
+        info->wave_entries = plan->dev[0].nmob_entries;
+    }
     return MZ_OK;
 }
 

@@ -126,15 +126,18 @@ struct PolF32C {
 // The forward substitution keeps y' in a 64-bit word per (slot, column) that
 // doubles as the readiness flag: the workspace is filled with a sentinel
 // first and a consumer polls until the word differs from it.
+//
+// int64: every 64-bit pattern is a possible value, INT64_MIN included, so a value
+// equal to the sentinel is published as kSentinel + 1 with an escape flag set for
+// its word first (kEscapes); a reader that sees kSentinel + 1 checks the flag.
+// This keeps the int64 transform exact modulo 2^64 for every input.
 struct MobI64 {
     using T = long long;
+    static constexpr bool kEscapes = true;
+    static constexpr bool kDW = false;
     static constexpr unsigned long long kSentinel = 0x8000000000000000ull;  // INT64_MIN
     static __device__ __forceinline__ T from_bits(unsigned long long b) { return (long long)b; }
-    static __device__ __forceinline__ unsigned long long to_bits(T v) {
-        // INT64_MIN itself is outside the documented value range; never publish the sentinel
-        unsigned long long b = (unsigned long long)v;
-        return b == kSentinel ? kSentinel + 1 : b;
-    }
+    static __device__ __forceinline__ unsigned long long to_bits(T v) { return (unsigned long long)v; }
     static __device__ __forceinline__ T add(T a, T b) {
         return (long long)((unsigned long long)a + (unsigned long long)b);
     }
@@ -151,12 +154,14 @@ struct MobI64 {
 
 struct MobF64 {
     using T = double;
+    static constexpr bool kEscapes = false;
+    static constexpr bool kDW = false;
     // a signalling-NaN pattern: fp64 arithmetic never produces it (results are quiet)
     static constexpr unsigned long long kSentinel = 0xFFF4000DEADBEEFull;
     static __device__ __forceinline__ T from_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
     static __device__ __forceinline__ unsigned long long to_bits(T v) {
         unsigned long long b = (unsigned long long)__double_as_longlong(v);
-        return b == kSentinel ? 0x7FF8000000000000ull : b;   // an input copied through unchanged
+        return b == kSentinel ? 0x7FF8000000000000ull : b;   // that NaN input copied through: another NaN
     }
     static __device__ __forceinline__ T add(T a, T b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ T sub(T a, T b) { return __dsub_rn(a, b); }
@@ -168,8 +173,9 @@ struct MobF64 {
     }
 };
 
-// F32C Moebius: pair planes in and out, fp64 prefixes in between.
+// F32C Moebius: pair planes in and out, fp64 prefixes in the forward substitution.
 struct MobF32C : MobF64 {
+    static constexpr bool kDW = true;
     static __device__ __forceinline__ T load_in(const void *p, int64_t i, int64_t nB) {
         const float *q = reinterpret_cast<const float *>(p);
         return __dadd_rn((double)q[i], (double)q[nB + i]);
@@ -180,6 +186,56 @@ struct MobF32C : MobF64 {
         float *q = reinterpret_cast<float *>(p);
         q[i] = hi;
         q[nB + i] = lo;
+    }
+    // the double-word copy of a prefix the forward substitution publishes for the
+    // later stages (leaf gather, V^-1), which run in compensated fp32
+    static __device__ __forceinline__ float2 to_dw(T v) {
+        float hi = __double2float_rn(v);
+        return make_float2(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
+    }
+};
+
+// ---------------------------------------------------------------- leaf gather policies
+// After the forward substitution has produced y' at every slot some other row reads,
+// the remaining rows (read by no other row) are a plain gather:
+// y'(x) = g(x) - sum_j y'(niv_j(x)) over the gather's tiled map, whose entry on x's own
+// chain is x's own slot, zeroed beforehand so that it adds nothing. Each policy gives
+// the word type W of the prefix array it reads and writes, the accumulator, and the
+// final subtraction from g(x).
+struct LeafI64 {
+    using W = long long;
+    using Acc = long long;
+    static __device__ __forceinline__ Acc acc_zero() { return 0; }
+    static __device__ __forceinline__ void acc_add(Acc &a, W v) {
+        a = (long long)((unsigned long long)a + (unsigned long long)v);
+    }
+    static __device__ __forceinline__ W result(const void *g, int64_t i, int64_t, const Acc &a) {
+        return (long long)((unsigned long long)reinterpret_cast<const long long *>(g)[i] - (unsigned long long)a);
+    }
+};
+
+struct LeafF64 {
+    using W = double;
+    using Acc = double;
+    static __device__ __forceinline__ Acc acc_zero() { return 0.0; }
+    static __device__ __forceinline__ void acc_add(Acc &a, W v) { a = __dadd_rn(a, v); }
+    static __device__ __forceinline__ W result(const void *g, int64_t i, int64_t, const Acc &a) {
+        return __dsub_rn(reinterpret_cast<const double *>(g)[i], a);
+    }
+};
+
+// Compensated fp32: Sum2 (as the zeta gather) over the double-word prefixes, then
+// g(x) minus the sum in double-word arithmetic.
+struct LeafF32C {
+    using W = float2;
+    using Acc = PolF32C::Acc;
+    static __device__ __forceinline__ Acc acc_zero() { return {0.f, 0.f}; }
+    static __device__ __forceinline__ void acc_add(Acc &a, W v) { PolF32C::acc_add(a, v); }
+    static __device__ __forceinline__ W result(const void *g, int64_t i, int64_t nB, const Acc &a) {
+        const float *q = reinterpret_cast<const float *>(g);
+        const DW s = two_sum(a.s, a.e);
+        const DW r = dw_add({q[i], q[nB + i]}, {-s.hi, -s.lo});
+        return make_float2(r.hi, r.lo);
     }
 };
 

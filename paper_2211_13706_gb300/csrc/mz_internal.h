@@ -89,6 +89,12 @@ struct DeviceSide {
     int32_t *mob_level = nullptr;  // [n] its level in the schedule
     int32_t kpad_max = 0;
     int32_t k_max = 0;
+    int64_t nmob = 0;              // rows of the Moebius schedule (U-level: the referenced rows only)
+    int32_t mob_kp_max = 0;        // longest row of the Moebius schedule (padded length)
+    int64_t nmob_entries = 0;      // their finite entries on other chains
+    uint8_t *slot_ref = nullptr;   // U-level schedule: [nslots] 1 = a slot another row reads
+    int32_t *row_leaf = nullptr;   // U-level schedule: [ntiles * 32] slot of a tile row no other row
+                                   // reads (computed by the leaf gather), -1 otherwise
 };
 
 }  // namespace mz
@@ -107,9 +113,10 @@ struct mz_plan {
     uint32_t *d_status = nullptr;   // device status word (MZ_OK / MZ_ERR_TIMEOUT)
     int device = -1;
     int num_sms = 0;
-    int32_t mob_blocks_per_sm = 2;  // one-thread-per-row wavefront: blocks of 128 threads per SM
-    int32_t mob_pace_ns = 500;      // wavefront pacing per level of distance (0: none)
+    int32_t mob_blocks_per_sm = 2;  // wavefront: resident blocks of 128 threads per SM (per lane group)
+    int32_t mob_pace_ns = 600;      // wavefront pacing per level of distance (0: none)
     int32_t gather_blocks_per_sm = 32;
+    int32_t mob_lanes = 32;         // batch-1 wavefront: lanes per row (1, 2, 4, 8, 16, 32)
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
     void *(*dev_alloc)(size_t, void *) = nullptr;

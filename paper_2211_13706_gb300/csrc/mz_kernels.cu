@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 
 #include "mz_arith.cuh"
 #include "mz_kernels.h"
@@ -53,7 +54,44 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_relaxed_u8(unsigned char *p, unsigned short v) {
+    asm volatile("st.relaxed.gpu.global.u8 [%0], %1;" ::"l"(p), "h"(v) : "memory");
+}
+__device__ __forceinline__ unsigned short ld_relaxed_u8(const unsigned char *p) {
+    unsigned short v;
+    asm volatile("ld.relaxed.gpu.global.u8 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void report(uint32_t *status, uint32_t code) { atomicCAS(status, 0u, code); }
+
+// Publishes y' word w (esc: its escape flag). A value whose bits equal the sentinel
+// (possible for int64 only) goes out as kSentinel + 1 after its escape flag is set
+// and fenced, so a reader that sees kSentinel + 1 and then fences sees the flag.
+template <class M>
+__device__ __forceinline__ void publish(unsigned long long *w, unsigned char *esc, typename M::T v) {
+    unsigned long long b = M::to_bits(v);
+    if constexpr (M::kEscapes) {
+        if (b == M::kSentinel) {
+            st_relaxed_u8(esc, 1);
+            __threadfence();
+            b = M::kSentinel + 1;
+        }
+    }
+    st_relaxed_u64(w, b);
+}
+
+// The value of a published y' word (esc: its escape flag).
+template <class M>
+__device__ __forceinline__ typename M::T decode(unsigned long long b, const unsigned char *esc) {
+    if constexpr (M::kEscapes) {
+        if (b == M::kSentinel + 1) {
+            __threadfence();
+            if (ld_relaxed_u8(esc)) return M::from_bits(M::kSentinel);
+        }
+    }
+    return M::from_bits(b);
+}
 
 // Wait until *flag != 0 (acquire). Gives up after `limit` polls, or early once
 // another wait has recorded an error; returns 0 then.
@@ -350,12 +388,22 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a
 }
 
 // ---------------------------------------------------------------- Moebius
+// y' init: the sentinel ("not yet published") at every slot the forward substitution
+// computes, 0 at zero slots and at the rows no other row reads (the leaf gather adds
+// the own-chain entry of such a row, its own slot, and it must add nothing); escape
+// flags and double-word copies cleared.
 template <class M>
-__global__ void k_mob_init(const int32_t *__restrict__ slot_node, int64_t nslots, int32_t B,
-                           unsigned long long *__restrict__ P) {
+__global__ void k_mob_init(const int32_t *__restrict__ slot_node, const uint8_t *__restrict__ slot_ref,
+                           int64_t nslots, int32_t B, unsigned long long *__restrict__ P,
+                           unsigned char *__restrict__ esc, float2 *__restrict__ Q) {
     const int64_t total = nslots * B;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-        P[i] = slot_node[i / B] < 0 ? 0ull : M::kSentinel;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / B;
+        const bool live = slot_node[s] >= 0 && (slot_ref == nullptr || slot_ref[s] != 0);
+        P[i] = live ? M::kSentinel : 0ull;
+        if (esc) esc[i] = 0;
+        if (Q) Q[i] = make_float2(0.f, 0.f);
+    }
 }
 
 template <class T>
@@ -363,21 +411,33 @@ __device__ __forceinline__ T shfl_xor_t(T v, int off) {
     return __shfl_xor_sync(0xffffffffu, v, off);
 }
 
+// Sleeps about ns nanoseconds. __nanosleep may sleep up to twice what it is asked, so a
+// long wait is a deadline on the SM clock (about 2 cycles per ns) checked between naps of
+// a quarter microsecond: a thread sleeping through many levels wakes on time.
+__device__ __forceinline__ void pace_until(int64_t ns) {
+    if (ns <= 0) return;
+    const long long end = clock64() + 2 * ns;
+    while (clock64() < end) __nanosleep(256);
+}
+
 // Sums the NV words v[j] = P[id[j]] into acc (or subtracts them, SUB) in column order, adding each one as
 // soon as it and all before it are present: columns are sorted by dependency
 // level, so words land roughly in order and when the last one lands only one
 // addition is left. The first missing word is polled, one request per round;
 // once it lands every later missing word is requested again in one round.
+// E: the escape flags aligned with P (int64 only).
 template <class M, int NV, bool SUB>
 __device__ __forceinline__ void sum_in_order(unsigned long long *v, const int32_t *id, const unsigned long long *P,
-                                             typename M::T &acc, uint32_t *status, int64_t limit) {
+                                             const unsigned char *E, typename M::T &acc, uint32_t *status,
+                                             int64_t limit) {
     const unsigned long long S = M::kSentinel;
     int next = 0;
     auto advance = [&]() {
 #pragma unroll
         for (int j = 0; j < NV; ++j)
             if (j == next && v[j] != S) {
-                acc = SUB ? M::sub(acc, M::from_bits(v[j])) : M::add(acc, M::from_bits(v[j]));
+                const typename M::T x = decode<M>(v[j], E + id[j]);
+                acc = SUB ? M::sub(acc, x) : M::add(acc, x);
                 next = j + 1;
             }
     };
@@ -434,8 +494,8 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
     // warp the rows stay consecutive. G lanes per row.
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    const int64_t tid = gwarp * 32 + lane;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = gwarp * 32 + lane;
     const int64_t grp = tid / G, ngrp = nthreads / G;
     const int b0 = (int)(tid % G);
     const int64_t B = (G == 1) ? 1 : a.B;
@@ -448,14 +508,7 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
         const int32_t level = a.mob_level[i];
         // The dependencies of this row sit at least one level lower; levels finish one
         // after the other, so sleep through the ones that must come first.
-        if (a.pace_ns > 0) {
-            int64_t ns = (int64_t)(level - done_level - 2) * a.pace_ns;
-            while (ns > 0) {
-                const unsigned q = ns > 500000 ? 500000u : (unsigned)ns;
-                __nanosleep(q);
-                ns -= q;
-            }
-        }
+        if (a.pace_ns > 0) pace_until((int64_t)(level - done_level - 2) * a.pace_ns);
         if (b0 == 0 && i + ngrp < a.n) {
             const char *nxt = reinterpret_cast<const char *>(a.Nm + a.mob_off[i + ngrp]);
             const int nkp = a.mob_kp[i + ngrp];
@@ -463,9 +516,10 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
         }
         const int64_t node = a.mob_node[i];
         const int64_t sout = a.mob_slot[i];
-        const bool publish = (i != a.withhold);
+        const bool publish_row = (i != a.withhold);
         for (int64_t b = b0; b < B; b += G) {
             unsigned long long *Pb = P + b;           // column b of every slot: Pb[s * B]
+            unsigned char *Eb = M::kEscapes ? a.esc + b : nullptr;
             const T gx = M::load_in(a.g, node * B + b, a.nB);
             unsigned long long vprev = ANTI ? ld_relaxed_u64(Pb + (sout - 1) * B) : 0ull;
             int32_t id[kChunk], nid[kChunk];
@@ -483,7 +537,7 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(Pb + sid[j]);
                 load_ids(row + c0 + kChunk, nid);
-                sum_in_order<M, kChunk, !ANTI>(v, sid, Pb, acc, a.status, a.spin_limit);
+                sum_in_order<M, kChunk, !ANTI>(v, sid, Pb, Eb, acc, a.status, a.spin_limit);
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) id[j] = nid[j];
             }
@@ -503,18 +557,22 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
 #pragma unroll
                     for (int j = 0; j < kChunk; ++j)
                         if (j == next && v[j] != S) {
-                            acc = ANTI ? M::add(acc, M::from_bits(v[j])) : M::sub(acc, M::from_bits(v[j]));
+                            const T x = decode<M>(v[j], Eb + sid[j]);
+                            acc = ANTI ? M::add(acc, x) : M::sub(acc, x);
                             next = j + 1;
                         }
                     if (ANTI && next == kChunk && vprev == S) vprev = ld_relaxed_u64(Pb + (sout - 1) * B);
                     if (next == kChunk && (!ANTI || vprev != S)) {
                         if (ANTI) {
-                            const T prev = M::from_bits(vprev);
+                            const T prev = decode<M>(vprev, Eb + (sout - 1) * B);
                             const T fx = M::sub(gx, M::add(acc, prev));
-                            if (publish) st_relaxed_u64(Pb + sout * B, M::to_bits(M::add(prev, fx)));
+                            if (publish_row) publish<M>(Pb + sout * B, Eb + sout * B, M::add(prev, fx));
                             M::store_out(a.f, node * B + b, a.nB, fx);
-                        } else if (publish) {
-                            st_relaxed_u64(Pb + sout * B, M::to_bits(acc));
+                        } else if (publish_row) {
+                            if constexpr (M::kDW) {
+                                if (a.Q) a.Q[sout * B + b] = M::to_dw(acc);   // read after this kernel ends
+                            }
+                            publish<M>(Pb + sout * B, Eb + sout * B, acc);
                         }
                         break;
                     }
@@ -537,6 +595,91 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
     }
 }
 
+// One function, U-level schedule, LR lanes per row: the row's chunks of 16 entries are
+// dealt to its lanes (chunk c to lane c mod LR), so all of a row's values are requested in
+// one round trip however late the row starts. Each lane adds its values as they land
+// (re-asking every missing one each round, bounded); the lanes' sums meet by shuffles and
+// the row's first lane publishes y'(x) = g(x) - sum. The row's own data (node, slot, g(x))
+// is requested before the waiting starts, so that only the shuffles, one subtraction and
+// the store follow the last value. (Measured on GB300, n = 2^20, k = 64: the full shuffle
+// tree after a warp barrier beat a tree over only the lanes holding chunks, a publishing
+// lane that waits on the last chunk itself, and partial sums met in shared memory.)
+template <class M, int LR>
+__global__ void __launch_bounds__(128) k_mob_wave_lr(MobArgs a) {
+    using T = typename M::T;
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int64_t tid = gwarp * 32 + lane;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t grp = tid / LR, ngrp = nthreads / LR;
+    const int sub = lane & (LR - 1);
+    const unsigned gmask = LR == 32 ? 0xffffffffu : (((1u << LR) - 1u) << (lane & ~(LR - 1)));
+    unsigned long long *P = a.P;
+    unsigned char *E = a.esc;
+    const unsigned long long S = M::kSentinel;
+    int32_t done_level = 0;
+    for (int64_t i = grp; i < a.n; i += ngrp) {
+        const int32_t *row = a.Nm + a.mob_off[i];
+        const int nch = a.mob_kp[i] / kChunk;
+        const int32_t level = a.mob_level[i];
+        if (a.pace_ns > 0) pace_until((int64_t)(level - done_level - 2) * a.pace_ns);
+        if (sub == 0 && i + ngrp < a.n) {
+            const char *nxt = reinterpret_cast<const char *>(a.Nm + a.mob_off[i + ngrp]);
+            const int nkp = a.mob_kp[i + ngrp];
+            for (int c = 0; c < nkp * 4; c += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + c));
+        }
+        int64_t sout = 0;
+        T gx = T(0);
+        if (sub == 0) {
+            const int64_t node = a.mob_node[i];
+            sout = a.mob_slot[i];
+            gx = M::load_in(a.g, node, a.nB);
+        }
+        T acc = T(0);
+        for (int c = sub; c < nch; c += LR) {
+            int32_t id[kChunk];
+            load_ids(row + c * kChunk, id);
+            unsigned long long v[kChunk];
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(P + id[j]);
+            int next = 0;
+            for (int64_t it = 0;; ++it) {
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j)
+                    if (j == next && v[j] != S) {
+                        acc = M::add(acc, decode<M>(v[j], E + id[j]));
+                        next = j + 1;
+                    }
+                if (next == kChunk) break;
+                if ((it & 127) == 127 && (ld_relaxed_u32(a.status) || it >= a.spin_limit)) {
+                    if (it >= a.spin_limit) report(a.status, MZ_ERR_TIMEOUT);
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        if (v[j] == S) v[j] = 0ull;
+                    continue;
+                }
+                // no pause between rounds: a sleep, however short, costs a round trip per level
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j)
+                    if (j >= next && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
+            }
+        }
+        if (LR > 1) {
+            __syncwarp(gmask);
+#pragma unroll
+            for (int off = LR / 2; off >= 1; off >>= 1) acc = M::add(acc, __shfl_xor_sync(gmask, acc, off));
+        }
+        if (sub == 0 && i != a.withhold) {
+            const T y = M::sub(gx, acc);
+            if constexpr (M::kDW) {
+                if (a.Q) a.Q[sout] = M::to_dw(y);   // read after this kernel ends
+            }
+            publish<M>(P + sout, E + sout, y);
+        }
+        done_level = level;
+    }
+}
+
 template <class M, bool ANTI>
 __global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
     using T = typename M::T;
@@ -545,80 +688,249 @@ __global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t B = a.B;
     unsigned long long *P = a.P;
+    unsigned char *E = a.esc;
     const unsigned long long SENT = M::kSentinel;
+    auto get = [&](int64_t w) { return decode<M>(wait_value(P + w, SENT, a.status, a.spin_limit), E + w); };
+    auto put = [&](int64_t w, T v) {
+        if constexpr (M::kDW) {
+            if (!ANTI && a.Q) a.Q[w] = M::to_dw(v);
+        }
+        publish<M>(P + w, E + w, v);
+    };
     for (int64_t i = warp; i < a.n; i += nwarps) {
         const int32_t *__restrict__ row = a.Nm + a.mob_off[i];
         const int k = a.mob_kp[i];
         const int64_t node = a.mob_node[i];
         const int64_t sout = a.mob_slot[i];
-        const bool publish = (i != a.withhold);
+        const bool publish_row = (i != a.withhold);
         if (B == 1) {
             T acc = T(0);
-            for (int c = lane; c < k; c += 32)
-                acc = M::add(acc, M::from_bits(wait_value(P + row[c], SENT, a.status, a.spin_limit)));
+            for (int c = lane; c < k; c += 32) acc = M::add(acc, get(row[c]));
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1) acc = M::add(acc, shfl_xor_t(acc, off));
             if (lane == 0) {
                 const T gx = M::load_in(a.g, node, a.nB);
                 if (ANTI) {
-                    const T prev = M::from_bits(wait_value(P + sout - 1, SENT, a.status, a.spin_limit));
+                    const T prev = get(sout - 1);
                     const T fx = M::sub(gx, M::add(acc, prev));
-                    if (publish) st_relaxed_u64(P + sout, M::to_bits(M::add(prev, fx)));
+                    if (publish_row) put(sout, M::add(prev, fx));
                     M::store_out(a.f, node, a.nB, fx);
-                } else if (publish) {
-                    st_relaxed_u64(P + sout, M::to_bits(M::sub(gx, acc)));
+                } else if (publish_row) {
+                    put(sout, M::sub(gx, acc));
                 }
             }
         } else if (B <= 32 && (B & (B - 1)) == 0) {
             const int bl = lane & (B - 1);
             const int cstep = 32 / B;
             T acc = T(0);
-            for (int c = lane / B; c < k; c += cstep)
-                acc = M::add(acc, M::from_bits(wait_value(P + (int64_t)row[c] * B + bl, SENT, a.status, a.spin_limit)));
+            for (int c = lane / B; c < k; c += cstep) acc = M::add(acc, get((int64_t)row[c] * B + bl));
             for (int off = 16; off >= B; off >>= 1) acc = M::add(acc, shfl_xor_t(acc, off));
             if (lane < B) {
                 const T gx = M::load_in(a.g, node * B + bl, a.nB);
                 if (ANTI) {
-                    const T prev = M::from_bits(wait_value(P + (sout - 1) * B + bl, SENT, a.status, a.spin_limit));
+                    const T prev = get((sout - 1) * B + bl);
                     const T fx = M::sub(gx, M::add(acc, prev));
-                    if (publish) st_relaxed_u64(P + sout * B + bl, M::to_bits(M::add(prev, fx)));
+                    if (publish_row) put(sout * B + bl, M::add(prev, fx));
                     M::store_out(a.f, node * B + bl, a.nB, fx);
-                } else if (publish) {
-                    st_relaxed_u64(P + sout * B + bl, M::to_bits(M::sub(gx, acc)));
+                } else if (publish_row) {
+                    put(sout * B + bl, M::sub(gx, acc));
                 }
             }
         } else {
             for (int64_t bl = lane; bl < B; bl += 32) {
                 T acc = T(0);
-                for (int c = 0; c < k; ++c)
-                    acc = M::add(acc, M::from_bits(wait_value(P + (int64_t)row[c] * B + bl, SENT, a.status, a.spin_limit)));
+                for (int c = 0; c < k; ++c) acc = M::add(acc, get((int64_t)row[c] * B + bl));
                 const T gx = M::load_in(a.g, node * B + bl, a.nB);
                 if (ANTI) {
-                    const T prev = M::from_bits(wait_value(P + (sout - 1) * B + bl, SENT, a.status, a.spin_limit));
+                    const T prev = get((sout - 1) * B + bl);
                     const T fx = M::sub(gx, M::add(acc, prev));
-                    if (publish) st_relaxed_u64(P + sout * B + bl, M::to_bits(M::add(prev, fx)));
+                    if (publish_row) put(sout * B + bl, M::add(prev, fx));
                     M::store_out(a.f, node * B + bl, a.nB, fx);
-                } else if (publish) {
-                    st_relaxed_u64(P + sout * B + bl, M::to_bits(M::sub(gx, acc)));
+                } else if (publish_row) {
+                    put(sout * B + bl, M::sub(gx, acc));
                 }
             }
         }
     }
 }
 
-template <class M>
+// ---- leaf gather (U-level schedule): the rows no other row reads, after the forward
+// substitution has finished every row they read: y'(x) = g(x) - sum over x's tile row of
+// the gather's map (own slot included, zeroed by the init). The same tiles and lane
+// layouts as the zeta gather.
+template <class L, class M>
+__device__ __forceinline__ typename L::W leaf_load(const MobArgs &a, const typename L::W *Pw, int64_t idx) {
+    typename L::W v = __ldg(Pw + idx);
+    if constexpr (M::kEscapes) {   // int64: a word of kSentinel + 1 with its escape flag set holds kSentinel
+        if ((unsigned long long)v == M::kSentinel + 1 && a.esc[idx]) v = (typename L::W)M::kSentinel;
+    }
+    return v;
+}
+
+template <class L, class M>
+__device__ __forceinline__ const typename L::W *leaf_words(const MobArgs &a) {
+    if constexpr (M::kDW) return reinterpret_cast<const typename L::W *>(a.Q);
+    else return reinterpret_cast<const typename L::W *>(a.P);
+}
+
+template <class L, class M>
+__device__ __forceinline__ void leaf_store(const MobArgs &a, int64_t idx, typename L::W v) {
+    if constexpr (M::kDW) a.Q[idx] = v;
+    else reinterpret_cast<typename L::W *>(a.P)[idx] = v;
+}
+
+template <class L, class M, int BT>
+__global__ void __launch_bounds__(kGatherThreads) k_mob_leaf(MobArgs a) {
+    using W = typename L::W;
+    using Acc = typename L::Acc;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t b0 = (int64_t)blockIdx.y * BT;
+    const int64_t B = a.B;
+    const W *__restrict__ Pw = leaf_words<L, M>(a);
+    for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
+        const int32_t lslot = a.row_leaf[tile * kTileRows + lane];
+        if (__all_sync(0xffffffffu, lslot < 0)) continue;   // no leaf row in this tile
+        const int k = a.tile_k[tile];
+        const int32_t *__restrict__ np = a.Nt + a.tile_off[tile] + lane;
+        Acc acc[BT];
+#pragma unroll
+        for (int u = 0; u < BT; ++u) acc[u] = L::acc_zero();
+        int c = 0;
+        for (; c + 8 <= k; c += 8) {
+            int32_t s[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s[u] = __ldcs(np + (int64_t)(c + u) * kTileRows);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int q = 0; q < BT; ++q)
+                    if (BT == 1 || b0 + q < B) L::acc_add(acc[q], leaf_load<L, M>(a, Pw, (int64_t)s[u] * B + b0 + q));
+        }
+        for (; c < k; ++c) {
+            const int32_t s = __ldcs(np + (int64_t)c * kTileRows);
+#pragma unroll
+            for (int q = 0; q < BT; ++q)
+                if (BT == 1 || b0 + q < B) L::acc_add(acc[q], leaf_load<L, M>(a, Pw, (int64_t)s * B + b0 + q));
+        }
+        if (lslot >= 0) {
+            const int64_t node = a.row_node[tile * kTileRows + lane];
+#pragma unroll
+            for (int q = 0; q < BT; ++q)
+                if (BT == 1 || b0 + q < B)
+                    leaf_store<L, M>(a, (int64_t)lslot * B + b0 + q, L::result(a.g, node * B + b0 + q, a.nB, acc[q]));
+        }
+    }
+}
+
+// Batched leaf gather (B > 1 a power of two): the lane layout of k_niv_gather_b.
+template <class L, class M, int G, bool NARROW>
+__global__ void __launch_bounds__(kGatherThreads, 2) k_mob_leaf_b(MobArgs a) {
+    using W = typename L::W;
+    using Acc = typename L::Acc;
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, b0 = lane % G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const W *__restrict__ Pw = leaf_words<L, M>(a);
+    const int64_t B = a.B;
+    const uint32_t Bu = (uint32_t)a.B;
+    for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
+        const int32_t *rl = a.row_leaf + tile * kTileRows;
+        if (__all_sync(0xffffffffu, rl[lane] < 0)) continue;   // no leaf row in this tile
+        const int k = a.tile_k[tile];
+        const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
+        for (int r = sub; r < kTileRows / 2; r += R) {
+            const int r2 = r + kTileRows / 2;
+            const int32_t ls = rl[r], ls2 = rl[r2];
+            if (ls < 0 && ls2 < 0) continue;                    // the whole lane group agrees
+            const int64_t node = a.row_node[tile * kTileRows + r];
+            const int64_t node2 = a.row_node[tile * kTileRows + r2];
+            for (int64_t b = b0; b < B; b += G) {
+                Acc acc = L::acc_zero(), acc2 = L::acc_zero();
+                int c = 0;
+                for (; c + 8 <= k; c += 8) {
+                    int32_t sl[8], sl2[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        sl[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r);
+                        sl2[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r2);
+                    }
+                    W v[8], v2[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (NARROW) {
+                            v[u] = leaf_load<L, M>(a, Pw, (int64_t)((uint32_t)sl[u] * Bu + (uint32_t)b));
+                            v2[u] = leaf_load<L, M>(a, Pw, (int64_t)((uint32_t)sl2[u] * Bu + (uint32_t)b));
+                        } else {
+                            v[u] = leaf_load<L, M>(a, Pw, (int64_t)sl[u] * B + b);
+                            v2[u] = leaf_load<L, M>(a, Pw, (int64_t)sl2[u] * B + b);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        L::acc_add(acc, v[u]);
+                        L::acc_add(acc2, v2[u]);
+                    }
+                }
+                for (; c < k; ++c) {
+                    L::acc_add(acc, leaf_load<L, M>(a, Pw, (int64_t)__ldg(nt + (int64_t)c * kTileRows + r) * B + b));
+                    L::acc_add(acc2, leaf_load<L, M>(a, Pw, (int64_t)__ldg(nt + (int64_t)c * kTileRows + r2) * B + b));
+                }
+                if (ls >= 0) leaf_store<L, M>(a, (int64_t)ls * B + b, L::result(a.g, node * B + b, a.nB, acc));
+                if (ls2 >= 0) leaf_store<L, M>(a, (int64_t)ls2 * B + b, L::result(a.g, node2 * B + b, a.nB, acc2));
+            }
+        }
+    }
+}
+
+// V^-1 (Sec. 3): f(x) = y'(x) - y'(next(x)), slot s - 1 being next(x) on the same
+// chain or the chain's zero slot. DWQ: from the double-word copies (F32C, U-level
+// schedule), in double-word arithmetic.
+template <class M, bool DWQ>
 __global__ void k_mob_diff(const int32_t *__restrict__ slot_node, int64_t nslots, int32_t B,
-                           const unsigned long long *__restrict__ P, void *f, int64_t nB) {
+                           const unsigned long long *__restrict__ P, const unsigned char *__restrict__ esc,
+                           const float2 *__restrict__ Q, void *f, int64_t nB) {
     const int64_t total = nslots * B;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i / B;
         const int32_t node = slot_node[s];
         if (node < 0) continue;
         const int64_t bl = i - s * B;
-        // slot s - 1 is next(x) on the same chain, or the chain's zero slot
-        const typename M::T y = M::from_bits(P[i]);
-        const typename M::T yp = M::from_bits(P[i - B]);
-        M::store_out(f, (int64_t)node * B + bl, nB, M::sub(y, yp));
+        const int64_t o = (int64_t)node * B + bl;
+        if constexpr (DWQ) {
+            const float2 y = Q[i], yp = Q[i - B];
+            const DW r = dw_add({y.x, y.y}, {-yp.x, -yp.y});
+            float *q = reinterpret_cast<float *>(f);
+            q[o] = r.hi;
+            q[nB + o] = r.lo;
+        } else {
+            const typename M::T y = decode<M>(P[i], esc + i);
+            const typename M::T yp = decode<M>(P[i - B], esc + i - B);
+            M::store_out(f, o, nB, M::sub(y, yp));
+        }
+    }
+}
+
+// Marks the slots read by a row of another chain: the rows of the forward substitution.
+__global__ void k_mark_referenced(const int32_t *__restrict__ Nt, const int64_t *__restrict__ tile_off,
+                                  const int32_t *__restrict__ tile_k, const int32_t *__restrict__ row_node,
+                                  int64_t ntiles, const int32_t *__restrict__ node_slot,
+                                  const int32_t *__restrict__ slot_node, uint8_t *__restrict__ slot_ref) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+        const int32_t x = row_node[tile * kTileRows + lane];
+        if (x < 0) continue;
+        const int32_t own = node_slot[x];
+        const int32_t *np = Nt + tile_off[tile] + lane;
+        for (int c = 0, k = tile_k[tile]; c < k; ++c) {
+            const int32_t s = np[(int64_t)c * kTileRows];
+            if (s != own && slot_node[s] >= 0) slot_ref[s] = 1;
+        }
     }
 }
 
@@ -685,23 +997,69 @@ cudaError_t launch_gather(int dtype, const GatherArgs &a, int num_sms, cudaStrea
     }
 }
 
-template <class M>
+template <class L, class M>
+static cudaError_t launch_leaf_t(const MobArgs &a, int64_t nslots, int num_sms, cudaStream_t st) {
+    const int warps_per_block = kGatherThreads / 32;
+    int64_t blocks = (a.ntiles + warps_per_block - 1) / warps_per_block;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms * std::max(1, a.gather_blocks_per_sm)));
+    if (a.B == 1) {
+        k_mob_leaf<L, M, 1><<<dim3((unsigned)blocks, 1), kGatherThreads, 0, st>>>(a);
+    } else if ((a.B & (a.B - 1)) == 0) {
+        const int G = a.B < 32 ? a.B : 32;
+        const dim3 grid((unsigned)blocks, 1);
+        const bool narrow = nslots * (int64_t)a.B <= (int64_t)0xffffffffll;
+#define MZ_LEAF_B(g)                                                                     \
+    (narrow ? k_mob_leaf_b<L, M, g, true><<<grid, kGatherThreads, 0, st>>>(a)              \
+            : k_mob_leaf_b<L, M, g, false><<<grid, kGatherThreads, 0, st>>>(a))
+        switch (G) {
+            case 2: MZ_LEAF_B(2); break;
+            case 4: MZ_LEAF_B(4); break;
+            case 8: MZ_LEAF_B(8); break;
+            case 16: MZ_LEAF_B(16); break;
+            default: MZ_LEAF_B(32); break;
+        }
+#undef MZ_LEAF_B
+    } else {
+        const unsigned gy = (unsigned)((a.B + 3) / 4);
+        k_mob_leaf<L, M, 4><<<dim3((unsigned)blocks, gy), kGatherThreads, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// Moebius launches. U-level schedule: init, forward substitution over the referenced
+// rows, leaf gather over the others, V^-1 (4 launches). Antichain schedule: init and
+// the forward substitution, which writes f itself (2 launches).
+template <class M, class L>
 static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, int64_t nslots, bool anti,
                                    int num_sms, cudaStream_t st, int *launches) {
     const int64_t total = nslots * a.B;
     const unsigned eblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 16));
-    k_mob_init<M><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P);
+    const bool dwq = M::kDW && !anti;      // F32C, U-level schedule: double-word copies for the later stages
+    float2 *Q = dwq ? a.Q : nullptr;
+    k_mob_init<M><<<eblocks, 256, 0, st>>>(slot_node, anti ? nullptr : a.slot_ref, nslots, a.B, a.P, a.esc, Q);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     mark_event(++*launches, st);
-    // persistent wavefront: every block resident (cooperative launch), one warp per row
+    // persistent wavefront: every block resident (cooperative launch)
     void *fn;
     int threads = 256;
     // rows per thread group: G = 1 for one function, G = min(B, 32) for a power-of-two batch
     const bool pow2 = (a.B & (a.B - 1)) == 0;
     const bool per_thread = pow2 && (int64_t)a.B * nslots < ((int64_t)1 << 31);
     int G = 1;
-    if (per_thread) {
+    const bool lanes = per_thread && a.B == 1 && !anti;   // one function: LR lanes per row
+    if (lanes) {
+        threads = 128;
+        G = a.lanes;
+        switch (G) {
+            case 1: fn = (void *)k_mob_wave_lr<M, 1>; break;
+            case 2: fn = (void *)k_mob_wave_lr<M, 2>; break;
+            case 8: fn = (void *)k_mob_wave_lr<M, 8>; break;
+            case 16: fn = (void *)k_mob_wave_lr<M, 16>; break;
+            case 32: fn = (void *)k_mob_wave_lr<M, 32>; break;
+            default: G = 4; fn = (void *)k_mob_wave_lr<M, 4>; break;
+        }
+    } else if (per_thread) {
         threads = 128;
         G = a.B < 32 ? a.B : 32;
 #define MZ_WAVE_G(g) (anti ? (void *)k_mob_wave_t<M, true, g> : (void *)k_mob_wave_t<M, false, g>)
@@ -717,6 +1075,8 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     } else {
         fn = anti ? (void *)k_mob_wave<M, true> : (void *)k_mob_wave<M, false>;
     }
+    MobArgs args = a;
+    args.Q = Q;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
     if (e != cudaSuccess) return e;
@@ -728,13 +1088,15 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     const int64_t rows_per_block = per_thread ? threads / G : threads / 32;
     blocks = std::min<int64_t>(blocks, (a.n + rows_per_block - 1) / rows_per_block);
     blocks = std::max<int64_t>(blocks, 1);
-    MobArgs args = a;
     void *params[] = {&args};
     e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(threads), params, 0, st);
     if (e != cudaSuccess) return e;
     mark_event(++*launches, st);
     if (!anti) {
-        k_mob_diff<M><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P, a.f, a.nB);
+        if ((e = launch_leaf_t<L, M>(args, nslots, num_sms, st)) != cudaSuccess) return e;
+        mark_event(++*launches, st);
+        if (dwq) k_mob_diff<M, true><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P, a.esc, Q, a.f, a.nB);
+        else k_mob_diff<M, false><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P, a.esc, nullptr, a.f, a.nB);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         mark_event(++*launches, st);
@@ -745,10 +1107,19 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
 cudaError_t launch_mobius(int dtype, const MobArgs &a, const int32_t *slot_node, int64_t nslots, bool anti,
                           int num_sms, cudaStream_t st, int *launches) {
     switch (dtype) {
-        case MZ_I64: return launch_mobius_t<MobI64>(a, slot_node, nslots, anti, num_sms, st, launches);
-        case MZ_F64: return launch_mobius_t<MobF64>(a, slot_node, nslots, anti, num_sms, st, launches);
-        default: return launch_mobius_t<MobF32C>(a, slot_node, nslots, anti, num_sms, st, launches);
+        case MZ_I64: return launch_mobius_t<MobI64, LeafI64>(a, slot_node, nslots, anti, num_sms, st, launches);
+        case MZ_F64: return launch_mobius_t<MobF64, LeafF64>(a, slot_node, nslots, anti, num_sms, st, launches);
+        default: return launch_mobius_t<MobF32C, LeafF32C>(a, slot_node, nslots, anti, num_sms, st, launches);
     }
+}
+
+cudaError_t launch_mark_referenced(const int32_t *Nt, const int64_t *tile_off, const int32_t *tile_k,
+                                   const int32_t *row_node, int64_t ntiles, const int32_t *node_slot,
+                                   const int32_t *slot_node, uint8_t *slot_ref, int num_sms, cudaStream_t st) {
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((ntiles + 7) / 8, (int64_t)num_sms * 16));
+    k_mark_referenced<<<(unsigned)blocks, 256, 0, st>>>(Nt, tile_off, tile_k, row_node, ntiles, node_slot, slot_node,
+                                                        slot_ref);
+    return cudaGetLastError();
 }
 
 }  // namespace mz

@@ -57,15 +57,29 @@ struct MobArgs {
     const int32_t *mob_slot;
     const int32_t *mob_level;   // level of each processed row
     int32_t pace_ns;            // sleep per level of distance before polling (0: none)
-    int64_t n;
+    int64_t n;                  // rows of the forward substitution's schedule
     int32_t B;
     const void *g;
     void *f;
-    int64_t nB;
+    int64_t nB;                 // (all nodes) * B: offset of the lo plane of F32C values
     unsigned long long *P;
     uint32_t *status;
     int64_t spin_limit;
     int64_t withhold;        // test hook: processing index whose y' is never published (-1: none)
+    unsigned char *esc;      // int64: [nslots][B] escape flags of words equal to the sentinel (else null)
+    float2 *Q;               // F32C, U-level schedule: [nslots][B] double-word copies of y' (else null)
+    const uint8_t *slot_ref; // U-level schedule: 1 at the slots the forward substitution computes
+                             // (read by another row); null: every slot (antichain schedule)
+    // leaf gather (U-level schedule): the zeta gather's tiles, and per tile row the slot
+    // of a row no other row reads (-1: a row of the forward substitution, or padding)
+    const int32_t *Nt;
+    const int64_t *tile_off;
+    const int32_t *tile_k;
+    const int32_t *row_node;
+    const int32_t *row_leaf;
+    int64_t ntiles;
+    int32_t gather_blocks_per_sm;
+    int32_t lanes;           // batch 1: lanes per row of the forward substitution (1, 2, 4, 8, 16 or 32)
 };
 
 // Device build (mz_build.cu).
@@ -147,6 +161,11 @@ cudaError_t launch_build_mob_rows_sparse(const BuildMobSparseArgs &a, int num_sm
 cudaError_t launch_build_niv(const BuildNivArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_build_tiles(const int32_t *N, int64_t n, int32_t k, int32_t *Nt, int num_sms, cudaStream_t st);
 cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream_t st);
+// Marks (slot_ref[s] = 1) every slot that some tile row holds as an entry of another
+// chain: the rows of the forward substitution. slot_ref is zeroed before the launch.
+cudaError_t launch_mark_referenced(const int32_t *Nt, const int64_t *tile_off, const int32_t *tile_k,
+                                   const int32_t *row_node, int64_t ntiles, const int32_t *node_slot,
+                                   const int32_t *slot_node, uint8_t *slot_ref, int num_sms, cudaStream_t st);
 
 ScanShape scan_shape(int64_t nslots, int32_t B);
 void mark_event(int i, cudaStream_t s);   // profiling hook of mz_set_launch_events

@@ -350,8 +350,12 @@ def test_launch_counts():
     plan.zeta(x)
     assert mz.mz_last_launch_count() == 2
     plan.mobius(x)
-    assert mz.mz_last_launch_count() == 3
+    assert mz.mz_last_launch_count() == 4            # init, forward substitution, leaf gather, V^-1
     plan.check()
+    anti = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
+    anti.mobius(x)
+    assert mz.mz_last_launch_count() == 2            # init, forward substitution writing f
+    anti.check()
 
 
 def test_argument_errors_on_device():
@@ -398,3 +402,35 @@ def test_autograd_backward_is_the_transpose():
             lm = (w * mz.MobiusFn.apply(mz.ZetaFn.apply(f - e, plan) * h, plan)).sum()
             fd = (lp - lm).item() / 2e-3
             assert abs(fd - got[i, b]) <= 1e-6 * max(1.0, abs(got[i, b]))
+
+
+# ----------------------------------------------------------------------------- lanes per row (one function)
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 32])
+def test_c1_wavefront_lanes_per_row(c1, lanes):
+    """One function with the U-level schedule: 1 to 32 lanes share a row of the forward
+    substitution (chunks of 16 entries dealt to the lanes, sums met by shuffles): int64
+    bit-exact and floats within tolerance under each."""
+    p, Z, mu = c1
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, build_transpose=True)
+    assert mz.mz_plan_tune(plan.handle, mobius_lanes=lanes)["mobius_lanes"] == lanes
+    f = values(p.n, 1, mz.MZ_I64, 31)[:, 0]
+    assert (run(plan, "mobius", f, mz.MZ_I64) == oracle.mobius(Z, f, "mu", mu=mu)).all()
+    assert (run(plan, "mobius_T", f, mz.MZ_I64) == oracle.mobius_T(Z, f, mu=mu)).all()
+    assert (run(plan, "mobius", run(plan, "zeta", f, mz.MZ_I64), mz.MZ_I64) == f).all()
+    for dtype in (mz.MZ_F64, mz.MZ_F32C):
+        g = values(p.n, 1, dtype, 32)[:, 0]
+        check_mobius(plan, Z, g if dtype == mz.MZ_F64 else _split(g.astype(np.float64)), dtype,
+                     f"lanes {lanes} mobius", mu=mu)
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 16])
+def test_c2_int64_round_trip_lanes_per_row(c2, lanes):
+    p, plan = c2
+    mz.mz_plan_tune(plan.handle, mobius_lanes=lanes)
+    f = values(p.n, 1, mz.MZ_I64, 33, "i64:1048576")[:, 0]
+    x = to_device(f, mz.MZ_I64)
+    back = plan.mobius(plan.zeta(x))
+    plan.check()
+    mz.mz_plan_tune(plan.handle, mobius_lanes=4)
+    assert torch.equal(back, x)
