@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
 // entry is a broadcast and the G loads of y' are contiguous. NARROW (nslots * B < 2^32):
 // y' offsets in 32-bit arithmetic, one instruction per address instead of a 64-bit multiply.
 template <class Pol, int G, bool NARROW>
-__global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_b(GatherArgs a) {
+__global__ void __launch_bounds__(kGatherThreads, 3) k_niv_gather_b(GatherArgs a) {
     using P_t = typename Pol::P_t;
     using Acc = typename Pol::Acc;
     constexpr int R = 32 / G;
@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_mob_leaf(MobArgs a) {
 
 // Batched leaf gather (B > 1 a power of two): the lane layout of k_niv_gather_b.
 template <class L, class M, int G, bool NARROW>
-__global__ void __launch_bounds__(kGatherThreads, 2) k_mob_leaf_b(MobArgs a) {
+__global__ void __launch_bounds__(kGatherThreads, 3) k_mob_leaf_b(MobArgs a) {
     using W = typename L::W;
     using Acc = typename L::Acc;
     constexpr int R = 32 / G;
