@@ -387,6 +387,86 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_niv_gather_b(GatherArgs a
     }
 }
 
+// Batched zeta gather for B a multiple of 32: a half-warp per row and two adjacent
+// columns per lane, so that one 16-byte load of y' serves two terms and one map entry and
+// one address serve both (rows r and r + 8 in half 0, r + 16 and r + 24 in half 1). The
+// compensated form runs 12-14 % faster than with k_niv_gather_b (256 posets, B = 32); the
+// same layout for the Moebius leaf gather was not faster (it holds more live registers,
+// so fewer warps fit), which keeps k_mob_leaf_b.
+template <class T>
+__device__ __forceinline__ T word_as(long long w) {
+    T v;
+    memcpy(&v, &w, sizeof(T));
+    return v;
+}
+
+template <class Pol, bool NARROW>
+__global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_h(GatherArgs a) {
+    using P_t = typename Pol::P_t;
+    using Acc = typename Pol::Acc;
+    static_assert(sizeof(P_t) == 8, "8-byte prefix words");
+    const int lane = threadIdx.x & 31;
+    const int half = lane >> 4, cp = lane & 15;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const P_t *__restrict__ P = reinterpret_cast<const P_t *>(a.P);
+    const int64_t B = a.B;
+    const uint32_t Bu = (uint32_t)a.B;
+    for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
+        const int k = a.tile_k[tile];
+        const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
+        for (int r0 = 0; r0 < 8; ++r0) {
+            const int ra = r0 + 16 * half, rb = ra + 8;
+            const int32_t na = a.row_node[tile * kTileRows + ra];
+            const int32_t nb = a.row_node[tile * kTileRows + rb];
+            for (int64_t b = 2 * cp; b < B; b += 32) {
+                const P_t *__restrict__ Pb = P + b;
+                Acc a0 = Pol::acc_zero(), a1 = Pol::acc_zero(), b0 = Pol::acc_zero(), b1 = Pol::acc_zero();
+                int c = 0;
+                for (; c + 8 <= k; c += 8) {
+                    int32_t sa[8], sb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        sa[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + ra);
+                        sb[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + rb);
+                    }
+                    longlong2 va[8], vb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const P_t *pa = NARROW ? Pb + (uint32_t)sa[u] * Bu : Pb + (int64_t)sa[u] * B;
+                        const P_t *pb = NARROW ? Pb + (uint32_t)sb[u] * Bu : Pb + (int64_t)sb[u] * B;
+                        va[u] = __ldg(reinterpret_cast<const longlong2 *>(pa));
+                        vb[u] = __ldg(reinterpret_cast<const longlong2 *>(pb));
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        Pol::acc_add(a0, word_as<P_t>(va[u].x));
+                        Pol::acc_add(a1, word_as<P_t>(va[u].y));
+                        Pol::acc_add(b0, word_as<P_t>(vb[u].x));
+                        Pol::acc_add(b1, word_as<P_t>(vb[u].y));
+                    }
+                }
+                for (; c < k; ++c) {
+                    const P_t *pa = P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + ra) * B + b;
+                    const P_t *pb = P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + rb) * B + b;
+                    Pol::acc_add(a0, __ldg(pa));
+                    Pol::acc_add(a1, __ldg(pa + 1));
+                    Pol::acc_add(b0, __ldg(pb));
+                    Pol::acc_add(b1, __ldg(pb + 1));
+                }
+                if (na >= 0) {
+                    Pol::store_out(a.g, (int64_t)na * B + b, a.nB, a0);
+                    Pol::store_out(a.g, (int64_t)na * B + b + 1, a.nB, a1);
+                }
+                if (nb >= 0) {
+                    Pol::store_out(a.g, (int64_t)nb * B + b, a.nB, b0);
+                    Pol::store_out(a.g, (int64_t)nb * B + b + 1, a.nB, b1);
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- Moebius
 // y' init: the sentinel ("not yet published") at every slot the forward substitution
 // computes, 0 at zero slots and at the rows no other row reads (the leaf gather adds
@@ -974,6 +1054,11 @@ static cudaError_t launch_gather_t(const GatherArgs &a, int num_sms, cudaStream_
 #define MZ_GATHER_B(g)                                                                   \
     (narrow ? k_niv_gather_b<Pol, g, true><<<grid, kGatherThreads, 0, st>>>(a)             \
             : k_niv_gather_b<Pol, g, false><<<grid, kGatherThreads, 0, st>>>(a))
+        if (G == 32) {               // B a multiple of 32: two columns per lane
+            if (narrow) k_niv_gather_h<Pol, true><<<grid, kGatherThreads, 0, st>>>(a);
+            else k_niv_gather_h<Pol, false><<<grid, kGatherThreads, 0, st>>>(a);
+            return cudaGetLastError();
+        }
         switch (G) {
             case 2: MZ_GATHER_B(2); break;
             case 4: MZ_GATHER_B(4); break;
