@@ -523,20 +523,33 @@ def time_batch_e2e(plan, x, steps, torch):
 
 
 def run_batch_workload(mz, wl, posets, steps, warmup, torch, dtypes=("f32c", "f64"), graph=True, e2e_steps=0,
-                       samples=None):
-    """Builds one plan for all posets, autotunes it and times each dtype (CUDA graph
-    replay); with e2e_steps also the end-to-end step from pinned host memory. samples:
-    a list of (poset index, column) whose inputs and outputs are copied to the host
-    (key "_samples", for the accuracy check of the CPU-baseline leg)."""
+                       samples=None, compare_builds=False):
+    """Builds one plan for all posets on the device, autotunes it and times each dtype (CUDA
+    graph replay); with e2e_steps also the end-to-end step from pinned host memory.
+    compare_builds: first builds the same plan on the host (timed, compared, freed).
+    samples: a list of (poset index, column) whose inputs and outputs are copied to the
+    host (key "_samples", for the accuracy check of the CPU-baseline leg)."""
     from paper_2211_13706_gb300 import autotune
     w = BATCH_WORKLOADS[wl]
+    spec = [(n, s_, d_, c) for n, s_, d_, c in posets]
+    host_s = host_info = None
+    if compare_builds:
+        t0 = time.perf_counter()
+        hp = mz.Plan.batch(spec)
+        host_s = time.perf_counter() - t0
+        host_info = hp.info
+        hp.close()
+        torch.cuda.empty_cache()
     t0 = time.perf_counter()
-    plan = mz.Plan.batch([(n, s_, d_, c) for n, s_, d_, c in posets])
+    plan = mz.Plan.batch(spec, device_build=True)
     build_s = time.perf_counter() - t0
     info = plan.info
     out = {"workload": w["desc"], "posets": info["components"], "n_total": info["n"], "k_total": info["k"],
            "nnz": info["nnz"], "max_ulevels": info["ulevels"], "wave_rows": info["wave_rows"], "batch": w["batch"],
-           "host_build_s": round(build_s, 1)}
+           "device_build_s": round(build_s, 2)}
+    if compare_builds:
+        out["host_build_s"] = round(host_s, 2)
+        out["same_plan_info"] = all(host_info[key] == info[key] for key in host_info)
     peak, peak_kind = load_peaks()
     n, k, B, nnz = info["n"], info["k"], w["batch"], info["nnz"]
     wave = (info["wave_rows"], info["wave_entries"])
@@ -903,7 +916,7 @@ def device_arm(args):
     if batch_posets is not None:
         plan.close()
         c4 = run_batch_workload(mz, "c4", batch_posets, max(3, args.steps // 4), 3, torch, e2e_steps=3,
-                                samples=c4_samples)
+                                samples=c4_samples, compare_builds=True)
 
     cpu = cpu_fast = accuracy = None
     if not args.no_cpu_baseline:
@@ -985,7 +998,7 @@ def batch_arm(args, posets):
             "config": {"workload": res["workload"], "posets": res["posets"], "n_total": res["n_total"],
                        "k_total": res["k_total"], "batch": res["batch"], "nnz": res["nnz"],
                        "max_ulevels": res["max_ulevels"], "l2": "inputs larger than L2",
-                       "units": "2*n*B node-values per step", "host_build_s": res["host_build_s"],
+                       "units": "2*n*B node-values per step", "device_build_s": res["device_build_s"],
                        "cuda_graph": main["cuda_graph"], "tuning": main["tuning"],
                        "parallelism": f"replicas x{world}"},
             "roofline": main["roofline"], "kernels": main["kernels"], "gather_alu": main.get("gather_alu"),

@@ -673,6 +673,7 @@ static mz_status upload_side_device(mz_plan *p, int side) {
         if ((st = tmp.put(&d_mrow, mrow.data(), mrow.size()))) return st;
         if (!H.sparse) {
             BuildMobArgs b;
+            std::memset(&b, 0, sizeof(b));
             b.N = d_N;
             b.k = (int32_t)k;
             b.mrow = d_mrow;
@@ -702,6 +703,331 @@ static mz_status upload_side_device(mz_plan *p, int side) {
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "device build");
     H.csr_ptr = std::vector<int64_t>();
     H.csr_adj = std::vector<int32_t>();
+    return MZ_OK;
+}
+
+// Device build of a plan of several posets with dense maps: the recurrence of Thm. 4 for
+// all posets in one dataflow launch over the union (a poset's rows are as wide as its own
+// number of chains), then the layouts of upload_side: tiles of 32 rows per poset, the
+// Moebius rows of all posets in one order (level, then poset, then row). Every entry is
+// decided by comparisons, so the plan equals the host build's entry for entry.
+static mz_status upload_batch_device(mz_plan *p, int side) {
+    std::vector<HostSide> &Hs = p->host[side];
+    DeviceSide &D = p->dev[side];
+    const size_t C = Hs.size();
+    const int64_t n = p->n_total(), nslots = p->slots_total(), K = p->chain_off.back();
+    const std::string who = side ? "dual: " : "";
+    const bool anti = (p->schedule == MZ_SCHED_ANTICHAIN);
+    D.n = n;
+    D.nslots = nslots;
+    D.k_max = 0;
+    D.kpad_max = 0;
+    int32_t maxh = 0;
+    for (const HostSide &H : Hs) {
+        D.k_max = std::max(D.k_max, H.k);
+        D.kpad_max = std::max<int32_t>(D.kpad_max, (H.k + 15) / 16 * 16);
+        maxh = std::max(maxh, H.nlevels);
+    }
+    mz_status st;
+    cudaError_t e;
+    {   // slot map, padded with -1 to a multiple of 64 entries
+        std::vector<int32_t> sn(((size_t)nslots + 63) / 64 * 64, -1);
+        for (size_t c = 0; c < C; ++c)
+            for (size_t q = 0; q < Hs[c].slot_node.size(); ++q) {
+                const int32_t v = Hs[c].slot_node[q];
+                sn[p->slot_off[c] + q] = v < 0 ? -1 : (int32_t)(v + p->node_off[c]);
+            }
+        if ((st = upload(p, &D.slot_node, sn.data(), sn.size()))) return st;
+    }
+    BuildScratch tmp(p);
+    // ---- the union's inputs of the recurrence
+    int64_t edges = 0, entries = 0;
+    for (const HostSide &H : Hs) {
+        edges += H.csr_ptr[(size_t)H.n];
+        entries += H.n * (int64_t)H.k;
+    }
+    std::vector<int64_t> ptr((size_t)n + 1), croff(C), cmoff(C);
+    std::vector<int32_t> adj((size_t)edges), node_slot((size_t)n), chain((size_t)n), comp((size_t)n),
+        topo_pos((size_t)n), base((size_t)K), ck(C), ckoff(C);
+    {
+        int64_t eo = 0, mo = 0;
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
+            const int64_t no = p->node_off[c], so = p->slot_off[c], ko = p->chain_off[c];
+            ck[c] = H.k;
+            ckoff[c] = (int32_t)ko;
+            croff[c] = no;
+            cmoff[c] = mo;
+            mo += H.n * (int64_t)H.k;
+            for (int64_t x = 0; x < H.n; ++x) {
+                ptr[(size_t)(no + x)] = eo + H.csr_ptr[(size_t)x];
+                node_slot[(size_t)(no + x)] = (int32_t)(H.node_slot[(size_t)x] + so);
+                chain[(size_t)(no + x)] = (int32_t)(H.chain_id[(size_t)x] + ko);
+                comp[(size_t)(no + x)] = (int32_t)c;
+                topo_pos[(size_t)(no + H.topo[(size_t)x])] = (int32_t)(no + x);
+            }
+            const int64_t ne = H.csr_ptr[(size_t)H.n];
+            for (int64_t q = 0; q < ne; ++q) adj[(size_t)(eo + q)] = (int32_t)(H.csr_adj[(size_t)q] + no);
+            eo += ne;
+            for (int32_t j = 0; j < H.k; ++j) base[(size_t)(ko + j)] = (int32_t)(H.chain_base[(size_t)j] + so);
+        }
+        ptr[(size_t)n] = eo;
+    }
+    // nodes bottom-up by height over all posets
+    std::vector<int32_t> order((size_t)n);
+    {
+        std::vector<int64_t> fill((size_t)maxh + 2, 0);
+        for (size_t c = 0; c < C; ++c)
+            for (int64_t x = 0; x < Hs[c].n; ++x) fill[(size_t)Hs[c].level[(size_t)x]]++;
+        for (size_t l = 1; l < fill.size(); ++l) fill[l] += fill[l - 1];
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
+            for (int64_t i = H.n - 1; i >= 0; --i) {
+                const int32_t x = H.topo[(size_t)i];
+                order[(size_t)fill[(size_t)H.level[(size_t)x] - 1]++] = (int32_t)(x + p->node_off[c]);
+            }
+        }
+    }
+    int64_t *d_ptr, *d_croff, *d_cmoff;
+    int32_t *d_adj, *d_order, *d_node_slot, *d_chain, *d_base, *d_pos, *d_comp, *d_ck, *d_ckoff;
+    if ((st = tmp.put(&d_ptr, ptr.data(), ptr.size())) || (st = tmp.put(&d_adj, adj.data(), adj.size())) ||
+        (st = tmp.put(&d_order, order.data(), order.size())) ||
+        (st = tmp.put(&d_node_slot, node_slot.data(), node_slot.size())) ||
+        (st = tmp.put(&d_chain, chain.data(), chain.size())) || (st = tmp.put(&d_base, base.data(), base.size())) ||
+        (st = tmp.put(&d_pos, topo_pos.data(), topo_pos.size())) || (st = tmp.put(&d_comp, comp.data(), comp.size())) ||
+        (st = tmp.put(&d_ck, ck.data(), ck.size())) || (st = tmp.put(&d_ckoff, ckoff.data(), ckoff.size())) ||
+        (st = tmp.put(&d_croff, croff.data(), croff.size())) || (st = tmp.put(&d_cmoff, cmoff.data(), cmoff.size())))
+        return st;
+    adj = std::vector<int32_t>();
+    int32_t *d_uslot = tmp.get<int32_t>((size_t)nslots);
+    int32_t *d_rowcnt = tmp.get<int32_t>((size_t)n);
+    uint32_t *d_small = tmp.get<uint32_t>(64);   // ticket, status, bad, -, nnz (u64 at word 4)
+    int32_t *d_N = tmp.get<int32_t>((size_t)entries);
+    uint32_t *d_ready = tmp.get<uint32_t>((size_t)n);
+    if (!d_uslot || !d_rowcnt || !d_small || !d_N || !d_ready) {
+        set_last_error("device allocation failed");
+        return MZ_ERR_OOM;
+    }
+    const uint32_t small_init[6] = {0u, 0u, 0xffffffffu, 0u, 0u, 0u};
+    // the map starts at slot 0 everywhere, so that no read can leave the slot range
+    if ((e = cudaMemset(d_uslot, 0xff, sizeof(int32_t) * nslots)) != cudaSuccess ||
+        (e = cudaMemcpy(d_small, small_init, sizeof(small_init), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(d_N, 0, sizeof(int32_t) * (size_t)entries)) != cudaSuccess ||
+        (e = cudaMemset(d_ready, 0, sizeof(uint32_t) * (size_t)n)) != cudaSuccess)
+        return cuda_fail(e, "build setup");
+    {
+        BuildNivArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.ptr = d_ptr;
+        a.adj = d_adj;
+        a.order = d_order;
+        a.node_slot = d_node_slot;
+        a.chain_id = d_chain;
+        a.base = d_base;
+        a.topo_pos = d_pos;
+        a.n = n;
+        a.k = D.k_max;
+        a.N = d_N;
+        a.uslot = d_uslot;
+        a.rowcnt = d_rowcnt;
+        a.ready = d_ready;
+        a.ticket = d_small;
+        a.status = d_small + 1;
+        a.bad = (int32_t *)(d_small + 2);
+        a.nnz = (unsigned long long *)(d_small + 4);
+        a.spin_limit = p->spin_limit;
+        a.comp = d_comp;
+        a.comp_k = d_ck;
+        a.comp_koff = d_ckoff;
+        a.comp_roff = d_croff;
+        a.comp_moff = d_cmoff;
+        if ((e = launch_build_niv(a, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "niv build launch");
+    }
+    uint32_t small[6];
+    if ((e = cudaMemcpy(small, d_small, sizeof(small), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "niv build");
+    if (small[1]) {
+        set_last_error(who + "device build: a bounded wait ran out");
+        return MZ_ERR_TIMEOUT;
+    }
+    if ((int32_t)small[2] >= 0) {   // the largest topological position (over the union) of a failing node
+        const int64_t g = (int32_t)small[2];
+        const size_t c = (size_t)(std::upper_bound(p->node_off.begin(), p->node_off.end(), g) - p->node_off.begin() - 1);
+        const HostSide &H = Hs[c];
+        const int32_t x = H.topo[(size_t)(g - p->node_off[c])];
+        set_last_error(who + "poset " + std::to_string(c) + ": chain " + std::to_string(H.chain_id[(size_t)x]) +
+                       " is not totally ordered at node " + std::to_string(x));
+        return MZ_ERR_BAD_CHAINS;
+    }
+    std::vector<int32_t> uslot((size_t)nslots), rowcnt((size_t)n);
+    if ((e = cudaMemcpy(uslot.data(), d_uslot, sizeof(int32_t) * nslots, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(rowcnt.data(), d_rowcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    for (size_t c = 0; c < C; ++c) {   // per poset: U levels, nnz (rows of poset c are global rows node_off[c] ..)
+        HostSide &H = Hs[c];
+        H.ulevel.assign((size_t)H.n, 0);
+        int64_t nnz = 0;
+        for (int64_t x = 0; x < H.n; ++x) {
+            H.ulevel[(size_t)x] = uslot[(size_t)(H.node_slot[(size_t)x] + p->slot_off[c])];
+            nnz += rowcnt[(size_t)(p->node_off[c] + x)];
+        }
+        H.nulevels = H.n ? *std::max_element(H.ulevel.begin(), H.ulevel.end()) + 1 : 0;
+        H.nnz = nnz;
+    }
+    // ---- tiles of 32 rows per poset (rows in slot order), as upload_side lays them out
+    std::vector<int32_t> rn_host;
+    {
+        int64_t nt = 0;
+        for (const HostSide &H : Hs) nt += (H.n + kTileRows - 1) / kTileRows;
+        D.ntiles = nt;
+        std::vector<int64_t> toff((size_t)nt), tmoff((size_t)nt);
+        std::vector<int32_t> tk((size_t)nt), trows((size_t)nt);
+        rn_host.assign((size_t)nt * kTileRows, -1);
+        int64_t t = 0, total = 0;
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
+            for (int64_t t0 = 0; t0 * kTileRows < H.n; ++t0, ++t) {
+                toff[(size_t)t] = total;
+                tk[(size_t)t] = H.k;
+                trows[(size_t)t] = (int32_t)std::min<int64_t>(kTileRows, H.n - t0 * kTileRows);
+                tmoff[(size_t)t] = cmoff[c] + t0 * kTileRows * (int64_t)H.k;
+                total += (int64_t)H.k * kTileRows;
+                for (int32_t q = 0; q < trows[(size_t)t]; ++q)
+                    rn_host[(size_t)(t * kTileRows + q)] =
+                        (int32_t)(H.row_node[(size_t)(t0 * kTileRows + q)] + p->node_off[c]);
+            }
+        }
+        D.Nt = (int32_t *)plan_alloc(p, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1));
+        if (!D.Nt) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        int64_t *d_tmoff;
+        int32_t *d_trows;
+        if ((st = upload(p, &D.tile_off, toff.data(), toff.size())) ||
+            (st = upload(p, &D.tile_k, tk.data(), tk.size())) ||
+            (st = upload(p, &D.row_node, rn_host.data(), rn_host.size())) ||
+            (st = tmp.put(&d_tmoff, tmoff.data(), tmoff.size())) || (st = tmp.put(&d_trows, trows.data(), trows.size())))
+            return st;
+        if ((e = launch_build_tiles_var(d_N, nt, d_tmoff, D.tile_k, d_trows, D.tile_off, D.Nt, p->num_sms, 0)) !=
+            cudaSuccess)
+            return cuda_fail(e, "tile build launch");
+    }
+    // ---- U-level schedule: the slots another chain's row reads
+    std::vector<uint8_t> ref;
+    if (!anti) {
+        D.slot_ref = (uint8_t *)plan_alloc(p, (size_t)nslots);
+        if (!D.slot_ref) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        if ((e = cudaMemset(D.slot_ref, 0, (size_t)nslots)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+        if ((e = launch_mark_referenced(D.Nt, D.tile_off, D.tile_k, D.row_node, D.ntiles, d_node_slot, D.slot_node,
+                                        D.slot_ref, p->num_sms, 0)) != cudaSuccess)
+            return cuda_fail(e, "reference marking launch");
+        ref.resize((size_t)nslots);
+        if ((e = cudaMemcpy(ref.data(), D.slot_ref, (size_t)nslots, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy");
+        std::vector<int32_t> rl(rn_host.size(), -1);
+        for (size_t q = 0; q < rn_host.size(); ++q)
+            if (rn_host[q] >= 0) {
+                const int32_t gs = node_slot[(size_t)rn_host[q]];
+                rl[q] = ref[(size_t)gs] ? -1 : gs;
+            }
+        if ((st = upload(p, &D.row_leaf, rl.data(), rl.size()))) return st;
+    }
+    // ---- Moebius rows: all posets in one order, by level, then poset, then row
+    {
+        auto in_schedule = [&](size_t c, int64_t r) {
+            return anti || ref[(size_t)(Hs[c].node_slot[(size_t)Hs[c].row_node[(size_t)r]] + p->slot_off[c])] != 0;
+        };
+        int32_t maxlvl = 0;
+        for (const HostSide &H : Hs) maxlvl = std::max(maxlvl, anti ? H.nlevels : H.nulevels);
+        std::vector<int64_t> cnt((size_t)maxlvl + 2, 0);
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
+            const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
+            for (int64_t r = 0; r < H.n; ++r)
+                if (in_schedule(c, r)) cnt[(size_t)lvl[(size_t)H.row_node[(size_t)r]] + 1]++;
+        }
+        for (size_t l = 1; l < cnt.size(); ++l) cnt[l] += cnt[l - 1];
+        const int64_t nm = cnt.back();
+        D.nmob = nm;
+        std::vector<std::pair<int32_t, int32_t>> ord((size_t)nm);
+        for (size_t c = 0; c < C; ++c) {
+            const HostSide &H = Hs[c];
+            const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
+            for (int64_t r = 0; r < H.n; ++r)
+                if (in_schedule(c, r)) ord[(size_t)cnt[(size_t)lvl[(size_t)H.row_node[(size_t)r]]]++] = {(int32_t)c, (int32_t)r};
+        }
+        std::vector<int64_t> moff((size_t)nm), rmoff((size_t)nm);
+        std::vector<int32_t> mkp((size_t)nm), mnode((size_t)nm), mslot((size_t)nm), mlevel((size_t)nm), rk((size_t)nm);
+        int64_t total = 0;
+        D.nmob_entries = 0;
+        D.mob_kp_max = 0;
+        for (int64_t i = 0; i < nm; ++i) {
+            const size_t c = (size_t)ord[(size_t)i].first;
+            const int64_t r = ord[(size_t)i].second;
+            const HostSide &H = Hs[c];
+            const std::vector<int32_t> &lvl = anti ? H.level : H.ulevel;
+            const int32_t x = H.row_node[(size_t)r];
+            const int32_t cntr = rowcnt[(size_t)(p->node_off[c] + r)];
+            mkp[(size_t)i] = std::max<int32_t>(16, (cntr - 1 + 15) / 16 * 16);
+            moff[(size_t)i] = total;
+            total += mkp[(size_t)i];
+            D.nmob_entries += cntr - 1;
+            D.mob_kp_max = std::max(D.mob_kp_max, mkp[(size_t)i]);
+            mnode[(size_t)i] = (int32_t)(x + p->node_off[c]);
+            mslot[(size_t)i] = (int32_t)(H.node_slot[(size_t)x] + p->slot_off[c]);
+            mlevel[(size_t)i] = lvl[(size_t)x];
+            rmoff[(size_t)i] = cmoff[c] + r * (int64_t)H.k;
+            rk[(size_t)i] = H.k;
+        }
+        const int32_t *key_slot = d_uslot;   // U levels by slot, -1 at zero slots
+        if (anti) {
+            std::vector<int32_t> ks((size_t)nslots, -1);
+            for (size_t c = 0; c < C; ++c)
+                for (int64_t x = 0; x < Hs[c].n; ++x)
+                    ks[(size_t)(Hs[c].node_slot[(size_t)x] + p->slot_off[c])] = Hs[c].level[(size_t)x];
+            int32_t *d_ks;
+            if ((st = tmp.put(&d_ks, ks.data(), ks.size()))) return st;
+            key_slot = d_ks;
+        }
+        D.Nm = (int32_t *)plan_alloc(p, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1));
+        if (!D.Nm) {
+            set_last_error("device allocation failed");
+            return MZ_ERR_OOM;
+        }
+        if ((e = cudaMemset(D.Nm, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1))) != cudaSuccess)
+            return cuda_fail(e, "cudaMemset");
+        int64_t *d_rmoff;
+        int32_t *d_rk;
+        if ((st = upload(p, &D.mob_off, moff.data(), moff.size())) || (st = upload(p, &D.mob_kp, mkp.data(), mkp.size())) ||
+            (st = upload(p, &D.mob_node, mnode.data(), mnode.size())) ||
+            (st = upload(p, &D.mob_slot, mslot.data(), mslot.size())) ||
+            (st = upload(p, &D.mob_level, mlevel.data(), mlevel.size())) ||
+            (st = tmp.put(&d_rmoff, rmoff.data(), rmoff.size())) || (st = tmp.put(&d_rk, rk.data(), rk.size())))
+            return st;
+        BuildMobArgs b;
+        std::memset(&b, 0, sizeof(b));
+        b.N = d_N;
+        b.k = D.k_max;
+        b.mrow = nullptr;
+        b.moff = D.mob_off;
+        b.mkp = D.mob_kp;
+        b.mslot = D.mob_slot;
+        b.key_slot = key_slot;
+        b.n = nm;
+        b.Nm = D.Nm;
+        b.row_moff = d_rmoff;
+        b.row_k = d_rk;
+        if ((e = launch_build_mob_rows(b, p->num_sms, 0)) != cudaSuccess) return cuda_fail(e, "row build launch");
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "device build");
+    for (HostSide &H : Hs) {
+        H.csr_ptr = std::vector<int64_t>();
+        H.csr_adj = std::vector<int32_t>();
+    }
     return MZ_OK;
 }
 
@@ -985,13 +1311,17 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
         set_last_error("device_build needs a device plan (host_only is set)");
         return MZ_ERR_INVALID_ARG;
     }
-    if (o.device_build && count != 1) {
-        set_last_error("device_build builds single-poset plans only");
-        return MZ_ERR_UNSUPPORTED;
-    }
+
     mz_status st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0, o.niv_format,
                                     o.device_build != 0);
     if (st) return st;
+    if (o.device_build && count > 1)
+        for (int side = 0; side < (p->has_dual ? 2 : 1); ++side)
+            for (const HostSide &H : p->host[side])
+                if (H.sparse) {
+                    set_last_error("device_build of several posets needs dense niv maps (k <= 512 chains each)");
+                    return MZ_ERR_UNSUPPORTED;
+                }
     p->schedule = o.mobius_schedule;
     p->host_only = o.host_only != 0;
     if (o.spin_limit > 0) p->spin_limit = o.spin_limit;
@@ -1014,7 +1344,9 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
             st = cuda_fail(e, "cudaMemset");
         }
         for (int side = 0; side < (p->has_dual ? 2 : 1) && st == MZ_OK; ++side)
-            st = p->host[side][0].niv_on_device ? upload_side_device(p.get(), side) : upload_side(p.get(), side);
+            st = !p->host[side][0].niv_on_device ? upload_side(p.get(), side)
+                 : p->components() > 1            ? upload_batch_device(p.get(), side)
+                                                  : upload_side_device(p.get(), side);
         if (st) {
             plan_free_all(p.get());
             return st;

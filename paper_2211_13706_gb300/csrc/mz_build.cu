@@ -69,7 +69,7 @@ __device__ bool wait_ready(const uint32_t *flag, uint32_t *status, int64_t limit
 template <int KJ>
 __global__ void __launch_bounds__(kBuildThreads) k_build_niv(BuildNivArgs a) {
     const int lane = threadIdx.x & 31;
-    const int32_t k = a.k;
+    int32_t k = a.k;
     int32_t base[KJ];
 #pragma unroll
     for (int j = 0; j < KJ; ++j) {
@@ -83,7 +83,23 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_niv(BuildNivArgs a) {
         t = __shfl_sync(kFull, t, 0);
         if ((int64_t)t >= a.n) break;
         const int32_t x = a.order[t];
-        const int32_t cx = a.chain_id[x], sx = a.node_slot[x];
+        int32_t cx = a.chain_id[x];
+        const int32_t sx = a.node_slot[x];
+        // the map of x's poset: rows of width k from N + moff on (row roff first)
+        int64_t roff = 0, moff = 0;
+        if (a.comp) {
+            const int32_t c = a.comp[x];
+            const int32_t koff = a.comp_koff[c];
+            k = a.comp_k[c];
+            roff = a.comp_roff[c];
+            moff = a.comp_moff[c];
+            cx -= koff;   // x's chain within its poset
+#pragma unroll
+            for (int j = 0; j < KJ; ++j) {
+                const int q = lane + 32 * j;
+                base[j] = q < k ? a.base[koff + q] : 0;
+            }
+        }
         int32_t cur[KJ];
 #pragma unroll
         for (int j = 0; j < KJ; ++j) cur[j] = base[j];
@@ -94,7 +110,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_niv(BuildNivArgs a) {
             bool ok = true;
             if (e + lane < e1) {
                 const int32_t z = a.adj[e + lane];
-                rz = (int64_t)a.node_slot[z] - a.chain_id[z] - 1;
+                rz = (int64_t)a.node_slot[z] - a.chain_id[z] - 1;   // over the union: the poset's rows are contiguous
                 ok = wait_ready(&a.ready[z], a.status, a.spin_limit);
             }
             // after a failed wait the rows are not read (the build reports the timeout)
@@ -103,7 +119,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_niv(BuildNivArgs a) {
             const int cnt = e1 - e < 32 ? (int)(e1 - e) : 32;
 #pragma unroll 2
             for (int q = 0; q < cnt; ++q) {
-                const int32_t *row = a.N + __shfl_sync(kFull, rz, q) * k;
+                const int32_t *row = a.N + moff + (__shfl_sync(kFull, rz, q) - roff) * k;
 #pragma unroll
                 for (int j = 0; j < KJ; ++j) {
                     const int c = lane + 32 * j;
@@ -132,8 +148,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_niv(BuildNivArgs a) {
         }
         u = __reduce_max_sync(kFull, u);
         finite = __reduce_add_sync(kFull, finite);
-        const int64_t r = (int64_t)sx - cx - 1;
-        int32_t *out = a.N + r * k;
+        const int64_t r = (int64_t)sx - a.chain_id[x] - 1;   // row over the union
+        int32_t *out = a.N + moff + (r - roff) * k;
 #pragma unroll
         for (int j = 0; j < KJ; ++j) {
             const int c = lane + 32 * j;
@@ -174,6 +190,33 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_tiles(const int32_t *N,
     }
 }
 
+// The same transpose for plans of several posets: per tile its rows' start in N, width
+// and number of rows.
+__global__ void __launch_bounds__(kBuildThreads) k_build_tiles_var(const int32_t *N, int64_t ntiles,
+                                                                  const int64_t *tile_moff, const int32_t *tile_k,
+                                                                  const int32_t *tile_rows, const int64_t *tile_off,
+                                                                  int32_t *Nt) {
+    __shared__ int32_t s[32][33];
+    const int tx = threadIdx.x & 31, ty0 = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int32_t k = tile_k[t], rows = tile_rows[t];
+        const int32_t *src = N + tile_moff[t];
+        int32_t *dst = Nt + tile_off[t];
+        for (int32_t q0 = 0; q0 < k; q0 += 32) {
+            for (int ty = ty0; ty < 32; ty += kBuildThreads / 32) {
+                const int32_t q = q0 + tx;
+                s[ty][tx] = (ty < rows && q < k) ? src[(int64_t)ty * k + q] : 0;
+            }
+            __syncthreads();
+            for (int ty = ty0; ty < 32; ty += kBuildThreads / 32) {
+                const int32_t q = q0 + ty;
+                if (q < k) dst[(int64_t)q * 32 + tx] = s[tx][ty];
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // One warp per row of the schedule. An entry's place is its rank under the order
 // (key, chain), the key being the level of the element in its slot; the host build
 // sorts by key stably over ascending chains, which is the same order.
@@ -181,17 +224,17 @@ template <int KJ>
 __global__ void __launch_bounds__(kBuildThreads) k_build_mob_rows(BuildMobArgs a) {
     __shared__ int32_t s_key[kBuildThreads / 32][32 * KJ];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int32_t k = a.k;
     const int64_t nwarps = (int64_t)gridDim.x * (kBuildThreads / 32);
     for (int64_t i = (int64_t)blockIdx.x * (kBuildThreads / 32) + w; i < a.n; i += nwarps) {
-        const int64_t r = a.mrow[i];
+        const int32_t k = a.row_k ? a.row_k[i] : a.k;
+        const int32_t *rowp = a.row_moff ? a.N + a.row_moff[i] : a.N + (int64_t)a.mrow[i] * k;
         const int32_t sx = a.mslot[i];
         int32_t slot[KJ], key[KJ];
         int cnt = 0;
 #pragma unroll
         for (int j = 0; j < KJ; ++j) {
             const int c = lane + 32 * j;
-            slot[j] = c < k ? a.N[r * k + c] : sx;
+            slot[j] = c < k ? rowp[c] : sx;
             key[j] = INT_MAX;
             if (c < k && slot[j] != sx) {
                 const int32_t kv = a.key_slot[slot[j]];
@@ -456,6 +499,14 @@ cudaError_t launch_build_niv(const BuildNivArgs &a, int num_sms, cudaStream_t st
         k_build_niv<KJ><<<(unsigned)blocks, kBuildThreads, 0, st>>>(a);
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_build_tiles_var(const int32_t *N, int64_t ntiles, const int64_t *tile_moff, const int32_t *tile_k,
+                                   const int32_t *tile_rows, const int64_t *tile_off, int32_t *Nt, int num_sms,
+                                   cudaStream_t st) {
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms * 8));
+    k_build_tiles_var<<<(unsigned)blocks, kBuildThreads, 0, st>>>(N, ntiles, tile_moff, tile_k, tile_rows, tile_off, Nt);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_tiles(const int32_t *N, int64_t n, int32_t k, int32_t *Nt, int num_sms, cudaStream_t st) {

@@ -102,6 +102,15 @@ struct BuildNivArgs {
     unsigned long long *nnz;    // total finite entries (zeroed)
     uint32_t *status;           // MZ_ERR_TIMEOUT after a wait ran out (zeroed)
     int64_t spin_limit;
+    // Plans of several posets (null for one): every node's poset, and per poset its
+    // number of chains, first chain, first row and the start of its rows in N (a poset's
+    // rows are as wide as its own number of chains). Rows, slots, chains and nodes are
+    // numbered over the union; k is then the widest poset's number of chains.
+    const int32_t *comp;        // [n]
+    const int32_t *comp_k;
+    const int32_t *comp_koff;
+    const int64_t *comp_roff;
+    const int64_t *comp_moff;
 };
 
 struct BuildMobArgs {
@@ -114,6 +123,8 @@ struct BuildMobArgs {
     const int32_t *key_slot;    // [n + k] sort key of the element in each slot, -1 at zero slots
     int64_t n;
     int32_t *Nm;                // out, zeroed before the launch
+    const int64_t *row_moff;    // plans of several posets: start of each schedule row's map row in N
+    const int32_t *row_k;       // and its width (null for one poset: mrow[i] * k, width k)
 };
 
 // Sparse map, one height level [lo, lo + cnt) of `order` per launch pair.
@@ -160,6 +171,11 @@ cudaError_t launch_build_tiles_sparse(const int64_t *row_beg, const int32_t *row
 cudaError_t launch_build_mob_rows_sparse(const BuildMobSparseArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_build_niv(const BuildNivArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_build_tiles(const int32_t *N, int64_t n, int32_t k, int32_t *Nt, int num_sms, cudaStream_t st);
+// Tiles of a plan of several posets: tile t holds tile_rows[t] rows of width tile_k[t] that
+// start at N + tile_moff[t], and goes to Nt + tile_off[t] (padding rows read slot 0).
+cudaError_t launch_build_tiles_var(const int32_t *N, int64_t ntiles, const int64_t *tile_moff, const int32_t *tile_k,
+                                   const int32_t *tile_rows, const int64_t *tile_off, int32_t *Nt, int num_sms,
+                                   cudaStream_t st);
 cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream_t st);
 // Marks (slot_ref[s] = 1) every slot that some tile row holds as an entry of another
 // chain: the rows of the forward substitution. slot_ref is zeroed before the launch.

@@ -21,8 +21,10 @@ def test_device_build_argument_checks():
         mz.mz_build(3, [0, 1], [1, 2], device_build=True, host_only=True)
     assert e.value.status == mz.MZ_ERR_INVALID_ARG
     p = pg.paper_example()
+    # several posets on the device: dense maps only (a 600-chain antichain keeps a sparse map)
+    q600 = pg.antichain_poset(600)
     with pytest.raises(mz.MzError) as e:
-        mz.mz_build_batch([(p.n, p.src, p.dst, None)] * 2, device_build=True)
+        mz.mz_build_batch([(p.n, p.src, p.dst, None), (q600.n, q600.src, q600.dst, None)], device_build=True)
     assert e.value.status == mz.MZ_ERR_UNSUPPORTED
     # a dense map on the device holds at most 512 chains: refused before any device work
     q = pg.antichain_poset(600)
@@ -201,3 +203,57 @@ def test_sparse_device_build_er_paper_scale():
         host.check()
         dev.check()
         assert torch.equal(a, b), op
+
+
+# ----------------------------------------------------------------------------- plans of several posets
+
+def _batch_posets():
+    ps = [pg.planted_chain_poset(2048, 256, 31, cross_deg=2), pg.paper_example(),
+          pg.planted_chain_poset(1500, 100, 32, cross_deg=2), pg.boolean_lattice(6),
+          pg.planted_chain_poset(3000, 7, 33, cross_deg=2), pg.chain_poset(700, seed=34),
+          pg.antichain_poset(40), pg.planted_chain_poset(1024, 4, 35, cross_p=4 / 1024),
+          pg.er_dag(500, 3, 36), pg.Poset(n=1, src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32))]
+    cids = [p.chain_id if p.name.startswith(("planted", "chain")) else None for p in ps]
+    return [(p.n, p.src, p.dst, c) for p, c in zip(ps, cids)]
+
+
+BATCH_INFO = INFO_KEYS + ("components", "wave_rows", "wave_entries")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("schedule", [mz.MZ_SCHED_ULEVEL, mz.MZ_SCHED_ANTICHAIN])
+def test_batch_device_build_equals_host_build(schedule):
+    """Ten posets of uneven n and k (1 to 256 chains) in one plan: the device build's plan
+    has the host build's info and exports, and every int64 transform is bit-identical."""
+    import torch
+    posets = _batch_posets()
+    host = mz.Plan.batch(posets, build_transpose=True, mobius_schedule=schedule)
+    dev = mz.Plan.batch(posets, build_transpose=True, mobius_schedule=schedule, device_build=True)
+    for key in BATCH_INFO:
+        assert host.info[key] == dev.info[key], key
+    for dual in (False, True):
+        for w in EXPORTS:
+            if w != mz.MZ_EXPORT_NIV:
+                assert np.array_equal(host.export(w, dual=dual), dev.export(w, dual=dual)), (w, dual)
+    n = host.info["n"]
+    for batch in (1, 32):
+        f = pg.function_values(n, batch, "i64:1000", 40 + batch)
+        x = torch.from_numpy(f if batch > 1 else f[:, 0].copy()).cuda()
+        for name in ("zeta", "mobius", "zeta_T", "mobius_T"):
+            a, b = getattr(host, name)(x), getattr(dev, name)(x)
+            host.check()
+            dev.check()
+            assert torch.equal(a, b), (name, batch)
+        assert torch.equal(dev.mobius(dev.zeta(x)), x)
+        dev.check()
+
+
+@pytest.mark.gpu
+def test_batch_device_build_names_the_poset_of_a_bad_chain():
+    posets = _batch_posets()
+    n, src, dst, _ = posets[4]
+    bad = np.arange(n, dtype=np.int32) % 2            # two "chains" that are not totally ordered
+    posets[4] = (n, src, dst, bad)
+    with pytest.raises(mz.MzError) as e:
+        mz.Plan.batch(posets, device_build=True)
+    assert e.value.status == mz.MZ_ERR_BAD_CHAINS and "poset 4" in str(e.value)
