@@ -109,10 +109,11 @@ typedef struct {
        map of the zeta gather and the rows of the Moebius schedule are then computed by
        kernels: for a dense map every node as soon as its children are done, for a sparse
        map one height level after the other. The plan is the one the host build makes,
-       entry for entry. Single posets only (mz_build; mz_build_batch returns
-       MZ_ERR_UNSUPPORTED), a dense map only with k <= 512 (niv_format 1 with more chains:
-       MZ_ERR_UNSUPPORTED); not with host_only (MZ_ERR_INVALID_ARG). A bounded wait that
-       runs out fails the build with MZ_ERR_TIMEOUT. */
+       entry for entry. A dense map only with k <= 512 (niv_format 1 with more chains:
+       MZ_ERR_UNSUPPORTED). mz_build_batch builds all its posets in one dataflow launch
+       when every one of them keeps a dense map (else MZ_ERR_UNSUPPORTED). Not with
+       host_only (MZ_ERR_INVALID_ARG). A bounded wait that runs out fails the build with
+       MZ_ERR_TIMEOUT. */
     int32_t device_build;
 } mz_build_opts;
 
