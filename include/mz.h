@@ -59,7 +59,10 @@ typedef enum {
     MZ_ERR_CUDA = 5,        /* a CUDA runtime call failed (mz_last_error() has the text) */
     MZ_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out (reported by mz_check) */
     MZ_ERR_UNSUPPORTED = 7, /* e.g. a transpose call on a plan built without the dual */
-    MZ_ERR_NO_DEVICE = 8    /* the plan was built host-only; transforms need a device plan */
+    MZ_ERR_NO_DEVICE = 8,   /* the plan was built host-only; transforms need a device plan */
+    MZ_ERR_BOUNDS = 9       /* MZ_DEBUG builds only: a kernel read an index from a plan table or the
+                               niv map that lies outside its array (reported by mz_check; the
+                               access was skipped) */
 } mz_status;
 
 typedef enum {
@@ -137,6 +140,15 @@ typedef struct {
                               reads (niv_j(x) = y for an x not on y's chain); the others are
                               computed afterwards by a gather. All n with MZ_SCHED_ANTICHAIN */
     int64_t wave_entries;  /* their finite niv entries on other chains */
+    int32_t lookahead_width; /* lanes per row segment of the look-ahead forward substitution
+                                (mz_tuning::mobius_lookahead; 0: the plan keeps no look-ahead
+                                tables): the smallest power of two >= 2 covering the longest
+                                row's chunks of 16 entries; a row computes up to
+                                min(32 / width, 8) - 1 of its dependencies itself */
+    int32_t lookahead_max_local; /* that number of dependencies a row computes itself */
+    int64_t wave_critical_rows; /* rows with a dependency exactly one level below them */
+    int64_t wave_critical_over; /* of those, rows with more such dependencies than they compute
+                                   themselves (they still wait a hop for the rest) */
 } mz_plan_info_t;
 /* For a plan of several posets (mz_build_batch) n, k, nnz and edges are totals over
    them and levels, ulevels, levels_T, ulevels_T and max_chain are maxima. */
@@ -286,9 +298,17 @@ typedef struct {
     int32_t mobius_lanes;         /* forward substitution of one function (batch 1): lanes sharing one
                                      row, a power of two up to 32 (default 32, or 1 when no row has
                                      more than 16 entries on other chains). The row's entries are
-                                     dealt to the lanes 16 at a time, each lane polls its own, and the
-                                     lane holding the last 16 adds the lanes' sums and publishes the
-                                     row; 0 keeps the current value */
+                                     dealt to the lanes 16 at a time, each lane polls and sums its
+                                     own, the lanes' sums meet in a shuffle tree and the row's first
+                                     lane publishes it; 0 keeps the current value */
+    int32_t mobius_lookahead;     /* forward substitution of one function with 32 lanes per row,
+                                     where the plan has the tables for it (U-level schedule, rows of
+                                     at most 256 entries): 1 = each row also computes, from their own
+                                     rows, up to 7 of its dependencies one level below it, so that it
+                                     waits only for words published two levels below; 2 = off (the
+                                     default); 0 keeps the current value. Results are the same bits
+                                     either way. */
+    int32_t reserved;             /* 0 */
 } mz_tuning;
 
 /* Sets the plan's launch shapes (results are unaffected); fills *current if non-NULL. */

@@ -27,7 +27,7 @@ import numpy as np
 from . import build as _build
 
 MZ_OK, MZ_ERR_INVALID_ARG, MZ_ERR_CYCLE, MZ_ERR_BAD_CHAINS, MZ_ERR_OOM, MZ_ERR_CUDA, \
-    MZ_ERR_TIMEOUT, MZ_ERR_UNSUPPORTED, MZ_ERR_NO_DEVICE = range(9)
+    MZ_ERR_TIMEOUT, MZ_ERR_UNSUPPORTED, MZ_ERR_NO_DEVICE, MZ_ERR_BOUNDS = range(10)
 MZ_I64, MZ_F64, MZ_F32C = 0, 1, 2
 MZ_SCHED_ULEVEL, MZ_SCHED_ANTICHAIN = 0, 1
 MZ_EXPORT_CHAIN_ID, MZ_EXPORT_CHAIN_POS, MZ_EXPORT_NIV, MZ_EXPORT_LEVEL, MZ_EXPORT_ULEVEL, MZ_EXPORT_TOPO = range(6)
@@ -108,10 +108,11 @@ def _opts(build_transpose, host_only, mobius_schedule, mobius_blocks_per_sm, mob
 
 class Tuning(ctypes.Structure):
     _fields_ = [("mobius_blocks_per_sm", ctypes.c_int32), ("mobius_pace_ns", ctypes.c_int32),
-                ("gather_blocks_per_sm", ctypes.c_int32), ("mobius_lanes", ctypes.c_int32)]
+                ("gather_blocks_per_sm", ctypes.c_int32), ("mobius_lanes", ctypes.c_int32),
+                ("mobius_lookahead", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
 class PlanInfo(ctypes.Structure):
@@ -120,14 +121,24 @@ class PlanInfo(ctypes.Structure):
                 ("ulevels", ctypes.c_int32), ("schedule", ctypes.c_int32), ("levels_T", ctypes.c_int32),
                 ("ulevels_T", ctypes.c_int32), ("max_chain", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("components", ctypes.c_int32), ("sparse", ctypes.c_int32), ("wave_rows", ctypes.c_int64),
-                ("wave_entries", ctypes.c_int64)]
+                ("wave_entries", ctypes.c_int64), ("lookahead_width", ctypes.c_int32),
+                ("lookahead_max_local", ctypes.c_int32), ("wave_critical_rows", ctypes.c_int64),
+                ("wave_critical_over", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 def _load():
-    path = _build.build()
+    # MZ_LIBRARY=debug loads the MZ_DEBUG build (bounds-checked kernels, poisoned
+    # workspaces); MZ_LIBRARY=<path> loads another build of the same C ABI.
+    which = os.environ.get("MZ_LIBRARY", "")
+    if which == "debug":
+        path = _build.build(debug=True)
+    elif which:
+        path = os.path.abspath(which)
+    else:
+        path = _build.build()
     lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
     vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
     lib.mz_build.argtypes = [i64, i64, vp, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
@@ -275,10 +286,11 @@ def mz_check(plan: int, stream: int = 0) -> None:
 
 
 def mz_plan_tune(plan: int, mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0,
-                 gather_blocks_per_sm: int = 0, mobius_lanes: int = 0) -> dict:
+                 gather_blocks_per_sm: int = 0, mobius_lanes: int = 0, mobius_lookahead: int = 0) -> dict:
     """mz_plan_tune: sets the given launch shapes (0 keeps one) and returns the current ones."""
     cur = Tuning()
-    want = Tuning(int(mobius_blocks_per_sm), int(mobius_pace_ns), int(gather_blocks_per_sm), int(mobius_lanes))
+    want = Tuning(int(mobius_blocks_per_sm), int(mobius_pace_ns), int(gather_blocks_per_sm), int(mobius_lanes),
+                  int(mobius_lookahead), 0)
     _check(lib.mz_plan_tune(plan, ctypes.byref(want), ctypes.byref(cur)), "mz_plan_tune")
     return cur.as_dict()
 

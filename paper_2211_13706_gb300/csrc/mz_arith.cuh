@@ -53,6 +53,60 @@ __device__ __forceinline__ DW dw_add(DW x, DW y) {
     return fast_two_sum(v.hi, w);
 }
 
+// ---------------------------------------------------------------- packed fp32 pairs
+// Two fp32 values in one 64-bit register pair (the first in the low half), operated on
+// by the paired fp32 instructions of sm_100 and later: one instruction, two IEEE
+// round-to-nearest operations, each with the result __fadd_rn / __fsub_rn gives, so a
+// pair runs the same error-free transformations as two scalar lanes, bit for bit.
+using f32x2 = unsigned long long;
+
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Knuth's TwoSum on both halves: s + e = a + b exactly.
+__device__ __forceinline__ void two_sum2(f32x2 a, f32x2 b, f32x2 &s, f32x2 &e) {
+    s = f2_add(a, b);
+    const f32x2 ap = f2_sub(s, b);
+    const f32x2 bp = f2_sub(s, ap);
+    e = f2_add(f2_sub(a, ap), f2_sub(b, bp));
+}
+
+// Dekker's Fast2Sum on both halves (|a| >= |b| or a == 0 in each).
+__device__ __forceinline__ void fast_two_sum2(f32x2 a, f32x2 b, f32x2 &s, f32x2 &e) {
+    s = f2_add(a, b);
+    e = f2_sub(b, f2_sub(s, a));
+}
+
+__device__ __forceinline__ f32x2 f2_neg(f32x2 a) { return a ^ 0x8000000080000000ull; }
+
+// dw_add on both halves: (xh, xl) + (yh, yl) -> (rh, rl).
+__device__ __forceinline__ void dw_add2(f32x2 xh, f32x2 xl, f32x2 yh, f32x2 yl, f32x2 &rh, f32x2 &rl) {
+    f32x2 sh, sl, th, tl, vh, vl;
+    two_sum2(xh, yh, sh, sl);
+    two_sum2(xl, yl, th, tl);
+    fast_two_sum2(sh, f2_add(sl, th), vh, vl);
+    fast_two_sum2(vh, f2_add(tl, vl), rh, rl);
+}
+
+// Sum2 accumulator of two columns (the fp32 pair form of PolF32C::Acc).
+struct Acc2 {
+    f32x2 s, e;
+};
+__device__ __forceinline__ void acc2_add(Acc2 &a, f32x2 hi, f32x2 lo) {
+    f32x2 t, err;
+    two_sum2(a.s, hi, t, err);
+    a.s = t;
+    a.e = f2_add(a.e, f2_add(err, lo));
+}
+
 // ---------------------------------------------------------------- value policies
 // Each policy gives:
 //   P_t            the element type of the zeta prefix array (8 bytes)

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 #include "mz_arith.cuh"
 #include "mz_kernels.h"
@@ -64,6 +65,46 @@ __device__ __forceinline__ unsigned short ld_relaxed_u8(const unsigned char *p) 
 }
 
 __device__ __forceinline__ void report(uint32_t *status, uint32_t code) { atomicCAS(status, 0u, code); }
+
+// Double-word copies of y' (F32C): word i = s * B + b as one float2, or, in column pairs
+// (pair: B even), hi at float 2 (i - (i & 1)) + (i & 1) and lo two floats further.
+__device__ __forceinline__ void dwq_store(float2 *Q, int64_t i, bool pair, float2 v) {
+    if (pair) {
+        float *q = reinterpret_cast<float *>(Q) + 2 * (i & ~1ll) + (i & 1);
+        q[0] = v.x;
+        q[2] = v.y;
+    } else {
+        Q[i] = v;
+    }
+}
+// MZ_DEBUG builds check every index a kernel takes from the niv map or a plan table before
+// using it: outside its range the status word gets MZ_ERR_BOUNDS and the index becomes a
+// safe one (slot 0, a zero slot; node -1, nothing written). Release builds compile the
+// checks away.
+__device__ __forceinline__ int32_t chk(int32_t v, int64_t lo, int64_t hi, int32_t safe, uint32_t *status) {
+#ifdef MZ_DEBUG
+    if (v < lo || v >= hi) {
+        report(status, MZ_ERR_BOUNDS);
+        return safe;
+    }
+#endif
+    return v;
+}
+// a niv map entry: a slot index in [0, nslots)
+__device__ __forceinline__ int32_t map_ldg(const int32_t *p, int64_t nslots, uint32_t *status) {
+    return chk(__ldg(p), 0, nslots, 0, status);
+}
+__device__ __forceinline__ int32_t map_ldcs(const int32_t *p, int64_t nslots, uint32_t *status) {
+    return chk(__ldcs(p), 0, nslots, 0, status);
+}
+
+__device__ __forceinline__ float2 dwq_load(const float2 *Q, int64_t i, bool pair) {
+    if (pair) {
+        const float *q = reinterpret_cast<const float *>(Q) + 2 * (i & ~1ll) + (i & 1);
+        return make_float2(q[0], q[2]);
+    }
+    return Q[i];
+}
 
 // Publishes y' word w (esc: its escape flag). A value whose bits equal the sentinel
 // (possible for int64 only) goes out as kSentinel + 1 after its escape flag is set
@@ -162,6 +203,8 @@ __global__ void __launch_bounds__(kScanThreads) k_chain_scan(ScanArgs a) {
             const int4 w = sv[q];
             sn[4 * q] = w.x; sn[4 * q + 1] = w.y; sn[4 * q + 2] = w.z; sn[4 * q + 3] = w.w;
         }
+#pragma unroll
+        for (int j = 0; j < kScanSeg; ++j) sn[j] = chk(sn[j], -1, a.nB / a.B, -1, a.status);
     } else {
 #pragma unroll
         for (int j = 0; j < kScanSeg; ++j) sn[j] = -1;
@@ -266,7 +309,18 @@ __global__ void __launch_bounds__(kScanThreads) k_chain_scan(ScanArgs a) {
 #pragma unroll
         for (int j = 0; j < kScanSeg; ++j) {
             const int64_t s = slot0 + j;
-            if (s < a.nslots) P[s * a.B + b] = (j < first_reset) ? Pol::scan_add(pre, vals[j]) : vals[j];
+            if (s < a.nslots) {
+                const P_t v = (j < first_reset) ? Pol::scan_add(pre, vals[j]) : vals[j];
+                if constexpr (std::is_same<Pol, PolF32C>::value) {
+                    if (a.pair_words) {   // hi of columns b, b ^ 1 side by side, then their lo
+                        float *q = reinterpret_cast<float *>(a.P) + 2 * (s * a.B + (b & ~1ll)) + (b & 1);
+                        q[0] = v.x;
+                        q[2] = v.y;
+                        continue;
+                    }
+                }
+                P[s * a.B + b] = v;
+            }
         }
     }
 }
@@ -293,14 +347,14 @@ __global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
         int32_t s[8];
         if (k >= 8) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) s[u] = __ldcs(np + (int64_t)u * kTileRows);
+            for (int u = 0; u < 8; ++u) s[u] = map_ldcs(np + (int64_t)u * kTileRows, a.nslots, a.status);
         }
         for (; c + 8 <= k; c += 8) {
             // the next 8 map entries are requested before this group's values are gathered
             int32_t sn[8];
             const bool more = c + 16 <= k;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) sn[u] = more ? __ldcs(np + (int64_t)(c + 8 + u) * kTileRows) : 0;
+            for (int u = 0; u < 8; ++u) sn[u] = more ? map_ldcs(np + (int64_t)(c + 8 + u) * kTileRows, a.nslots, a.status) : 0;
 #pragma unroll
             for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -310,12 +364,12 @@ __global__ void __launch_bounds__(kGatherThreads) k_niv_gather(GatherArgs a) {
             for (int u = 0; u < 8; ++u) s[u] = sn[u];
         }
         for (; c < k; ++c) {
-            const int32_t s = __ldcs(np + (int64_t)c * kTileRows);
+            const int32_t s = map_ldcs(np + (int64_t)c * kTileRows, a.nslots, a.status);
 #pragma unroll
             for (int q = 0; q < BT; ++q)
                 if (BT == 1 || b0 + q < a.B) Pol::acc_add(acc[q], __ldg(P + (int64_t)s * a.B + b0 + q));
         }
-        const int32_t node = a.row_node[tile * kTileRows + lane];
+        const int32_t node = chk(a.row_node[tile * kTileRows + lane], -1, a.nB / a.B, -1, a.status);
         if (node >= 0) {
 #pragma unroll
             for (int q = 0; q < BT; ++q)
@@ -346,8 +400,8 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_niv_gather_b(GatherArgs a
         const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
         for (int r = sub; r < kTileRows / 2; r += R) {
             const int r2 = r + kTileRows / 2;
-            const int32_t node = a.row_node[tile * kTileRows + r];
-            const int32_t node2 = a.row_node[tile * kTileRows + r2];
+            const int32_t node = chk(a.row_node[tile * kTileRows + r], -1, a.nB / a.B, -1, a.status);
+            const int32_t node2 = chk(a.row_node[tile * kTileRows + r2], -1, a.nB / a.B, -1, a.status);
             for (int64_t b = b0; b < B; b += G) {
                 const P_t *__restrict__ Pb = P + b;
                 Acc acc = Pol::acc_zero(), acc2 = Pol::acc_zero();
@@ -356,8 +410,8 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_niv_gather_b(GatherArgs a
                     int32_t sl[8], sl2[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        sl[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r);
-                        sl2[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r2);
+                        sl[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + r, a.nslots, a.status);
+                        sl2[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + r2, a.nslots, a.status);
                     }
                     P_t v[8], v2[8];
 #pragma unroll
@@ -377,8 +431,8 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_niv_gather_b(GatherArgs a
                     }
                 }
                 for (; c < k; ++c) {
-                    Pol::acc_add(acc, __ldg(P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + r) * B + b));
-                    Pol::acc_add(acc2, __ldg(P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + r2) * B + b));
+                    Pol::acc_add(acc, __ldg(P + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + r, a.nslots, a.status) * B + b));
+                    Pol::acc_add(acc2, __ldg(P + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + r2, a.nslots, a.status) * B + b));
                 }
                 if (node >= 0) Pol::store_out(a.g, (int64_t)node * B + b, a.nB, acc);
                 if (node2 >= 0) Pol::store_out(a.g, (int64_t)node2 * B + b, a.nB, acc2);
@@ -417,8 +471,8 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_h(GatherArgs a
         const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
         for (int r0 = 0; r0 < 8; ++r0) {
             const int ra = r0 + 16 * half, rb = ra + 8;
-            const int32_t na = a.row_node[tile * kTileRows + ra];
-            const int32_t nb = a.row_node[tile * kTileRows + rb];
+            const int32_t na = chk(a.row_node[tile * kTileRows + ra], -1, a.nB / a.B, -1, a.status);
+            const int32_t nb = chk(a.row_node[tile * kTileRows + rb], -1, a.nB / a.B, -1, a.status);
             for (int64_t b = 2 * cp; b < B; b += 32) {
                 const P_t *__restrict__ Pb = P + b;
                 Acc a0 = Pol::acc_zero(), a1 = Pol::acc_zero(), b0 = Pol::acc_zero(), b1 = Pol::acc_zero();
@@ -427,8 +481,8 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_h(GatherArgs a
                     int32_t sa[8], sb[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        sa[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + ra);
-                        sb[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + rb);
+                        sa[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + ra, a.nslots, a.status);
+                        sb[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + rb, a.nslots, a.status);
                     }
                     longlong2 va[8], vb[8];
 #pragma unroll
@@ -447,8 +501,8 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_h(GatherArgs a
                     }
                 }
                 for (; c < k; ++c) {
-                    const P_t *pa = P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + ra) * B + b;
-                    const P_t *pb = P + (int64_t)__ldg(nt + (int64_t)c * kTileRows + rb) * B + b;
+                    const P_t *pa = P + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + ra, a.nslots, a.status) * B + b;
+                    const P_t *pb = P + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + rb, a.nslots, a.status) * B + b;
                     Pol::acc_add(a0, __ldg(pa));
                     Pol::acc_add(a1, __ldg(pa + 1));
                     Pol::acc_add(b0, __ldg(pb));
@@ -461,6 +515,76 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_h(GatherArgs a
                 if (nb >= 0) {
                     Pol::store_out(a.g, (int64_t)nb * B + b, a.nB, b0);
                     Pol::store_out(a.g, (int64_t)nb * B + b + 1, a.nB, b1);
+                }
+            }
+        }
+    }
+}
+
+// The compensated gather of k_niv_gather_h on packed fp32 pairs: the chain scan stores
+// the prefixes of columns b and b + 1 (b even) as hi_b, hi_b+1, lo_b, lo_b+1, so one
+// 16-byte load gives the pair of hi parts and the pair of lo parts, and every step of
+// Sum2 runs once for both columns (sums bit-identical to k_niv_gather_h, in half the fp32
+// instructions).
+template <bool NARROW>
+__global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_h2(GatherArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int half = lane >> 4, cp = lane & 15;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const ulonglong2 *__restrict__ P = reinterpret_cast<const ulonglong2 *>(a.P);   // one per column pair
+    const int64_t B = a.B, B2 = a.B / 2;
+    const uint32_t B2u = (uint32_t)(a.B / 2);
+    float *g = reinterpret_cast<float *>(a.g);
+    for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
+        const int k = a.tile_k[tile];
+        const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
+        for (int r0 = 0; r0 < 8; ++r0) {
+            const int ra = r0 + 16 * half, rb = ra + 8;
+            const int32_t na = chk(a.row_node[tile * kTileRows + ra], -1, a.nB / a.B, -1, a.status);
+            const int32_t nb = chk(a.row_node[tile * kTileRows + rb], -1, a.nB / a.B, -1, a.status);
+            for (int64_t bp = cp; bp < B2; bp += 16) {        // column pair bp: columns 2 bp, 2 bp + 1
+                const ulonglong2 *__restrict__ Pb = P + bp;
+                Acc2 x{0ull, 0ull}, y{0ull, 0ull};
+                int c = 0;
+                for (; c + 8 <= k; c += 8) {
+                    int32_t sa[8], sb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        sa[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + ra, a.nslots, a.status);
+                        sb[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + rb, a.nslots, a.status);
+                    }
+                    ulonglong2 va[8], vb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        va[u] = __ldg(NARROW ? Pb + (uint32_t)sa[u] * B2u : Pb + (int64_t)sa[u] * B2);
+                        vb[u] = __ldg(NARROW ? Pb + (uint32_t)sb[u] * B2u : Pb + (int64_t)sb[u] * B2);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        acc2_add(x, va[u].x, va[u].y);
+                        acc2_add(y, vb[u].x, vb[u].y);
+                    }
+                }
+                for (; c < k; ++c) {
+                    const ulonglong2 va = __ldg(Pb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + ra, a.nslots, a.status) * B2);
+                    const ulonglong2 vb = __ldg(Pb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + rb, a.nslots, a.status) * B2);
+                    acc2_add(x, va.x, va.y);
+                    acc2_add(y, vb.x, vb.y);
+                }
+                // normalise once, as PolF32C::store_out: hi and lo planes, both columns at once
+                f32x2 hi, lo;
+                if (na >= 0) {
+                    two_sum2(x.s, x.e, hi, lo);
+                    const int64_t i = (int64_t)na * B + 2 * bp;
+                    *reinterpret_cast<f32x2 *>(g + i) = hi;
+                    *reinterpret_cast<f32x2 *>(g + a.nB + i) = lo;
+                }
+                if (nb >= 0) {
+                    two_sum2(y.s, y.e, hi, lo);
+                    const int64_t i = (int64_t)nb * B + 2 * bp;
+                    *reinterpret_cast<f32x2 *>(g + i) = hi;
+                    *reinterpret_cast<f32x2 *>(g + a.nB + i) = lo;
                 }
             }
         }
@@ -554,13 +678,15 @@ __device__ __forceinline__ void sum_in_order(unsigned long long *v, const int32_
 // thread's next row is prefetched into L1 at the start of each row.
 constexpr int kChunk = 16;
 
-__device__ __forceinline__ void load_ids(const int32_t *p, int32_t *id) {
+__device__ __forceinline__ void load_ids(const int32_t *p, int32_t *id, int64_t nslots, uint32_t *status) {
     const int4 *q = reinterpret_cast<const int4 *>(p);
 #pragma unroll
     for (int t = 0; t < kChunk / 4; ++t) {
         const int4 w = __ldg(q + t);
         id[4 * t] = w.x; id[4 * t + 1] = w.y; id[4 * t + 2] = w.z; id[4 * t + 3] = w.w;
     }
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) id[j] = chk(id[j], 0, nslots, 0, status);
 }
 
 // G lanes per row (G = 1 for one function, G = min(B, 32) for B functions, B a
@@ -594,8 +720,8 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
             const int nkp = a.mob_kp[i + ngrp];
             for (int c = 0; c < nkp * 4; c += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + c));
         }
-        const int64_t node = a.mob_node[i];
-        const int64_t sout = a.mob_slot[i];
+        const int64_t node = chk(a.mob_node[i], 0, a.nB / a.B, 0, a.status);
+        const int64_t sout = chk(a.mob_slot[i], 0, a.nslots, 0, a.status);
         const bool publish_row = (i != a.withhold);
         for (int64_t b = b0; b < B; b += G) {
             unsigned long long *Pb = P + b;           // column b of every slot: Pb[s * B]
@@ -603,7 +729,7 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
             const T gx = M::load_in(a.g, node * B + b, a.nB);
             unsigned long long vprev = ANTI ? ld_relaxed_u64(Pb + (sout - 1) * B) : 0ull;
             int32_t id[kChunk], nid[kChunk];
-            load_ids(row, id);
+            load_ids(row, id, a.nslots, a.status);
             // U form: acc runs as g(x) - (sum of the values so far), so that once the last
             // value lands one subtraction is left; the antichain form sums, as it needs
             // y'(next(x)) apart.
@@ -616,7 +742,7 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
                 for (int j = 0; j < kChunk; ++j) sid[j] = (int32_t)((int64_t)id[j] * B);
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(Pb + sid[j]);
-                load_ids(row + c0 + kChunk, nid);
+                load_ids(row + c0 + kChunk, nid, a.nslots, a.status);
                 sum_in_order<M, kChunk, !ANTI>(v, sid, Pb, Eb, acc, a.status, a.spin_limit);
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) id[j] = nid[j];
@@ -650,7 +776,7 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
                             M::store_out(a.f, node * B + b, a.nB, fx);
                         } else if (publish_row) {
                             if constexpr (M::kDW) {
-                                if (a.Q) a.Q[sout * B + b] = M::to_dw(acc);   // read after this kernel ends
+                                if (a.Q) dwq_store(a.Q, sout * B + b, a.pair_q, M::to_dw(acc));   // read after this kernel ends
                             }
                             publish<M>(Pb + sout * B, Eb + sout * B, acc);
                         }
@@ -711,14 +837,14 @@ __global__ void __launch_bounds__(128) k_mob_wave_lr(MobArgs a) {
         int64_t sout = 0;
         T gx = T(0);
         if (sub == 0) {
-            const int64_t node = a.mob_node[i];
-            sout = a.mob_slot[i];
+            const int64_t node = chk(a.mob_node[i], 0, a.nB, 0, a.status);   // B == 1
+            sout = chk(a.mob_slot[i], 0, a.nslots, 0, a.status);
             gx = M::load_in(a.g, node, a.nB);
         }
         T acc = T(0);
         for (int c = sub; c < nch; c += LR) {
             int32_t id[kChunk];
-            load_ids(row + c * kChunk, id);
+            load_ids(row + c * kChunk, id, a.nslots, a.status);
             unsigned long long v[kChunk];
 #pragma unroll
             for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(P + id[j]);
@@ -760,6 +886,180 @@ __global__ void __launch_bounds__(128) k_mob_wave_lr(MobArgs a) {
     }
 }
 
+// The forward substitution with a look-ahead of one level (one function, U-level
+// schedule, a warp per row). A row x at level L reads rows of levels up to L - 1; the
+// ones at L - 1 (its critical dependencies, the tail of its sorted row) would cost a
+// full store-to-poll hop after their own hop. Instead, the warp computes up to
+// min(32 / W, 8) - 1 of them itself from their own rows, which read only levels up to
+// L - 2, so that a row waits for words published two levels below it: one hop per two
+// levels on the critical path. The warp is cut into segments of W lanes (W >= chunks
+// of the longest row): segment 0 holds x, segment t >= 1 the t-th computed dependency,
+// lane c of a segment the row's chunk c of 16 entries.
+//
+// Every row's value, wherever computed, is formed in one fixed order, that of
+// k_mob_wave_lr<M, 32>: each chunk summed in entry order from 0, the chunks' sums met by
+// a 32-lane butterfly (here: the adds of zero that lanes >= W would contribute, then a
+// W-lane butterfly, which is the same sequence of operations on every lane < W), and
+// y'(x) = g(x) - sum. A computed dependency therefore has the bits its own warp
+// publishes, and the results equal those of the kernel without look-ahead bit for bit.
+// The row withheld by the test hook is never computed here either (it is polled).
+template <class M, int W>
+__global__ void __launch_bounds__(128) k_mob_wave_la(MobArgs a) {
+    using T = typename M::T;
+    constexpr int kSeg = 32 / W;
+    constexpr int kMaxLocal = (kSeg - 1) < 7 ? (kSeg - 1) : 7;   // computed dependencies per row
+    const int lane = threadIdx.x & 31;
+    const int seg = lane / W, c = lane % W;
+    const int64_t gwarp = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long *P = a.P;
+    unsigned char *E = a.esc;
+    const unsigned long long S = M::kSentinel;
+    int32_t done_level = 0;
+    for (int64_t i = gwarp; i < a.n; i += nwarps) {
+        const int32_t *row = a.Nm + a.mob_off[i];
+        const int kp = a.mob_kp[i];
+        const int32_t level = a.mob_level[i];
+        const int m = min((int)a.mob_ncrit[i], kMaxLocal);
+        const int pos0 = kp - m;                 // entries pos0 .. kp - 1: computed here
+        // the row's words are published two levels below it, each level taking about half a hop
+        if (a.pace_ns > 0) pace_until((int64_t)(level - done_level - 3) * a.pace_ns);
+        if (lane == 0 && i + nwarps < a.n) {
+            const char *nxt = reinterpret_cast<const char *>(a.Nm + a.mob_off[i + nwarps]);
+            const int nkp = a.mob_kp[i + nwarps];
+            for (int q = 0; q < nkp * 4; q += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + q));
+        }
+        // this segment's row: x itself, or the dependency at entry pos0 + seg - 1
+        int64_t rs = -1;
+        if (seg == 0) {
+            rs = i;
+        } else if (seg <= m) {
+            const int32_t d = chk(a.slot_sched[chk(row[pos0 + seg - 1], 0, a.nslots, 0, a.status)], -1, a.n, -1,
+                                  a.status);
+            rs = (d >= 0 && d != a.withhold) ? d : -1;
+        }
+        const unsigned lm = __ballot_sync(0xffffffffu, c == 0 && seg >= 1 && rs >= 0);
+        int snch = 0;
+        const int32_t *srow = nullptr;
+        T sg = T(0);
+        int64_t sout = 0;
+        if (rs >= 0) {
+            srow = a.Nm + a.mob_off[rs];
+            snch = a.mob_kp[rs] / kChunk;
+            if (c == 0) {
+                sg = M::load_in(a.g, chk(a.mob_node[rs], 0, a.nB, 0, a.status), a.nB);   // B == 1
+                if (seg == 0) sout = chk(a.mob_slot[i], 0, a.nslots, 0, a.status);
+            }
+        }
+        // entry q of x (segment 0) is computed here when q >= pos0 and its segment has a row
+        auto local = [&](int q) { return q >= pos0 && ((lm >> ((q - pos0 + 1) * W)) & 1u); };
+        // Phase 1: each lane sums its chunk in entry order up to the first computed entry
+        // (segment 0) or to its end (the dependencies, whose words are all two levels down).
+        T acc = T(0);
+        int32_t id[kChunk];
+        unsigned long long v[kChunk];
+        int next = 0, stop = 0;
+        const bool has = rs >= 0 && c < snch;
+        if (has) {
+            load_ids(srow + c * kChunk, id, a.nslots, a.status);
+            stop = kChunk;
+            if (seg == 0) stop = max(0, min(kChunk, pos0 - c * kChunk));
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j)
+                v[j] = (seg == 0 && local(c * kChunk + j)) ? S : ld_relaxed_u64(P + id[j]);
+            for (int64_t it = 0; next < stop; ++it) {
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j)
+                    if (j == next && j < stop && v[j] != S) {
+                        acc = M::add(acc, decode<M>(v[j], E + id[j]));
+                        next = j + 1;
+                    }
+                if (next >= stop) break;
+                if ((it & 127) == 127 && (ld_relaxed_u32(a.status) || it >= a.spin_limit)) {
+                    if (it >= a.spin_limit) report(a.status, MZ_ERR_TIMEOUT);
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        if (j < stop && v[j] == S) v[j] = 0ull;
+                    continue;
+                }
+                // All 32 lanes poll here (in the kernel without look-ahead only the lanes of
+                // one row do): each asks for its first missing word only, and once that lands
+                // for every later missing one in one round, which keeps the L1 requests of a
+                // round to one per lane.
+                const unsigned long long *addr = P;
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j)
+                    if (j == next) addr = P + id[j];
+                const unsigned long long got = ld_relaxed_u64(addr);
+                if (got != S) {
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j) {
+                        if (j == next) v[j] = got;
+                        else if (j > next && j < stop && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
+                    }
+                }
+            }
+        }
+        // Phase 2: the dependencies' values (segments 1 .. m), handed to every lane.
+        __syncwarp();
+        T t = acc;
+        if (W < 32) t = M::add(t, T(0));
+#pragma unroll
+        for (int off = W / 2; off >= 1; off >>= 1) t = M::add(t, __shfl_xor_sync(0xffffffffu, t, off));
+        const T yd = M::sub(sg, t);
+        T crit[kMaxLocal > 0 ? kMaxLocal : 1];
+#pragma unroll
+        for (int u = 0; u < kMaxLocal; ++u) crit[u] = __shfl_sync(0xffffffffu, yd, (u + 1) * W);
+        // Phase 3: segment 0 finishes its chunks in entry order, computed entries from crit,
+        // the others (the withheld row) polled.
+        if (seg == 0 && has && next < kChunk) {
+            for (int64_t it = 0;; ++it) {
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j)
+                    if (j == next) {
+                        const int q = c * kChunk + j;
+                        if (local(q)) {
+                            T x = crit[0];
+#pragma unroll
+                            for (int u = 1; u < kMaxLocal; ++u)
+                                if (q - pos0 == u) x = crit[u];
+                            acc = M::add(acc, x);
+                            next = j + 1;
+                        } else if (v[j] != S) {
+                            acc = M::add(acc, decode<M>(v[j], E + id[j]));
+                            next = j + 1;
+                        }
+                    }
+                if (next == kChunk) break;
+                if ((it & 127) == 127 && (ld_relaxed_u32(a.status) || it >= a.spin_limit)) {
+                    if (it >= a.spin_limit) report(a.status, MZ_ERR_TIMEOUT);
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j)
+                        if (v[j] == S) v[j] = 0ull;
+                    continue;
+                }
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j)
+                    if (j >= next && v[j] == S && !local(c * kChunk + j)) v[j] = ld_relaxed_u64(P + id[j]);
+            }
+        }
+        // x's value: the same tree over segment 0
+        __syncwarp();
+        T s0 = seg == 0 ? acc : T(0);
+        if (W < 32) s0 = M::add(s0, T(0));
+#pragma unroll
+        for (int off = W / 2; off >= 1; off >>= 1) s0 = M::add(s0, __shfl_xor_sync(0xffffffffu, s0, off));
+        if (lane == 0 && i != a.withhold) {
+            const T y = M::sub(sg, s0);
+            if constexpr (M::kDW) {
+                if (a.Q) a.Q[sout] = M::to_dw(y);   // read after this kernel ends
+            }
+            publish<M>(P + sout, E + sout, y);
+        }
+        done_level = level;
+    }
+}
+
 template <class M, bool ANTI>
 __global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
     using T = typename M::T;
@@ -773,19 +1073,20 @@ __global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
     auto get = [&](int64_t w) { return decode<M>(wait_value(P + w, SENT, a.status, a.spin_limit), E + w); };
     auto put = [&](int64_t w, T v) {
         if constexpr (M::kDW) {
-            if (!ANTI && a.Q) a.Q[w] = M::to_dw(v);
+            if (!ANTI && a.Q) dwq_store(a.Q, w, a.pair_q, M::to_dw(v));
         }
         publish<M>(P + w, E + w, v);
     };
     for (int64_t i = warp; i < a.n; i += nwarps) {
         const int32_t *__restrict__ row = a.Nm + a.mob_off[i];
         const int k = a.mob_kp[i];
-        const int64_t node = a.mob_node[i];
-        const int64_t sout = a.mob_slot[i];
+        const int64_t node = chk(a.mob_node[i], 0, a.nB / a.B, 0, a.status);
+        const int64_t sout = chk(a.mob_slot[i], 0, a.nslots, 0, a.status);
         const bool publish_row = (i != a.withhold);
+        auto ent = [&](int c) { return (int64_t)chk(row[c], 0, a.nslots, 0, a.status); };
         if (B == 1) {
             T acc = T(0);
-            for (int c = lane; c < k; c += 32) acc = M::add(acc, get(row[c]));
+            for (int c = lane; c < k; c += 32) acc = M::add(acc, get(ent(c)));
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1) acc = M::add(acc, shfl_xor_t(acc, off));
             if (lane == 0) {
@@ -803,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
             const int bl = lane & (B - 1);
             const int cstep = 32 / B;
             T acc = T(0);
-            for (int c = lane / B; c < k; c += cstep) acc = M::add(acc, get((int64_t)row[c] * B + bl));
+            for (int c = lane / B; c < k; c += cstep) acc = M::add(acc, get(ent(c) * B + bl));
             for (int off = 16; off >= B; off >>= 1) acc = M::add(acc, shfl_xor_t(acc, off));
             if (lane < B) {
                 const T gx = M::load_in(a.g, node * B + bl, a.nB);
@@ -819,7 +1120,7 @@ __global__ void __launch_bounds__(256) k_mob_wave(MobArgs a) {
         } else {
             for (int64_t bl = lane; bl < B; bl += 32) {
                 T acc = T(0);
-                for (int c = 0; c < k; ++c) acc = M::add(acc, get((int64_t)row[c] * B + bl));
+                for (int c = 0; c < k; ++c) acc = M::add(acc, get(ent(c) * B + bl));
                 const T gx = M::load_in(a.g, node * B + bl, a.nB);
                 if (ANTI) {
                     const T prev = get((sout - 1) * B + bl);
@@ -870,7 +1171,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_mob_leaf(MobArgs a) {
     const int64_t B = a.B;
     const W *__restrict__ Pw = leaf_words<L, M>(a);
     for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
-        const int32_t lslot = a.row_leaf[tile * kTileRows + lane];
+        const int32_t lslot = chk(a.row_leaf[tile * kTileRows + lane], -1, a.nslots, -1, a.status);
         if (__all_sync(0xffffffffu, lslot < 0)) continue;   // no leaf row in this tile
         const int k = a.tile_k[tile];
         const int32_t *__restrict__ np = a.Nt + a.tile_off[tile] + lane;
@@ -881,7 +1182,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_mob_leaf(MobArgs a) {
         for (; c + 8 <= k; c += 8) {
             int32_t s[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) s[u] = __ldcs(np + (int64_t)(c + u) * kTileRows);
+            for (int u = 0; u < 8; ++u) s[u] = map_ldcs(np + (int64_t)(c + u) * kTileRows, a.nslots, a.status);
 #pragma unroll
             for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -889,13 +1190,13 @@ __global__ void __launch_bounds__(kGatherThreads) k_mob_leaf(MobArgs a) {
                     if (BT == 1 || b0 + q < B) L::acc_add(acc[q], leaf_load<L, M>(a, Pw, (int64_t)s[u] * B + b0 + q));
         }
         for (; c < k; ++c) {
-            const int32_t s = __ldcs(np + (int64_t)c * kTileRows);
+            const int32_t s = map_ldcs(np + (int64_t)c * kTileRows, a.nslots, a.status);
 #pragma unroll
             for (int q = 0; q < BT; ++q)
                 if (BT == 1 || b0 + q < B) L::acc_add(acc[q], leaf_load<L, M>(a, Pw, (int64_t)s * B + b0 + q));
         }
         if (lslot >= 0) {
-            const int64_t node = a.row_node[tile * kTileRows + lane];
+            const int64_t node = chk(a.row_node[tile * kTileRows + lane], 0, a.nB / a.B, 0, a.status);
 #pragma unroll
             for (int q = 0; q < BT; ++q)
                 if (BT == 1 || b0 + q < B)
@@ -924,10 +1225,10 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_mob_leaf_b(MobArgs a) {
         const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
         for (int r = sub; r < kTileRows / 2; r += R) {
             const int r2 = r + kTileRows / 2;
-            const int32_t ls = rl[r], ls2 = rl[r2];
+            const int32_t ls = chk(rl[r], -1, a.nslots, -1, a.status), ls2 = chk(rl[r2], -1, a.nslots, -1, a.status);
             if (ls < 0 && ls2 < 0) continue;                    // the whole lane group agrees
-            const int64_t node = a.row_node[tile * kTileRows + r];
-            const int64_t node2 = a.row_node[tile * kTileRows + r2];
+            const int64_t node = chk(a.row_node[tile * kTileRows + r], -1, a.nB / a.B, 0, a.status);
+            const int64_t node2 = chk(a.row_node[tile * kTileRows + r2], -1, a.nB / a.B, 0, a.status);
             for (int64_t b = b0; b < B; b += G) {
                 Acc acc = L::acc_zero(), acc2 = L::acc_zero();
                 int c = 0;
@@ -935,8 +1236,8 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_mob_leaf_b(MobArgs a) {
                     int32_t sl[8], sl2[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        sl[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r);
-                        sl2[u] = __ldg(nt + (int64_t)(c + u) * kTileRows + r2);
+                        sl[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + r, a.nslots, a.status);
+                        sl2[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + r2, a.nslots, a.status);
                     }
                     W v[8], v2[8];
 #pragma unroll
@@ -956,11 +1257,86 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_mob_leaf_b(MobArgs a) {
                     }
                 }
                 for (; c < k; ++c) {
-                    L::acc_add(acc, leaf_load<L, M>(a, Pw, (int64_t)__ldg(nt + (int64_t)c * kTileRows + r) * B + b));
-                    L::acc_add(acc2, leaf_load<L, M>(a, Pw, (int64_t)__ldg(nt + (int64_t)c * kTileRows + r2) * B + b));
+                    L::acc_add(acc, leaf_load<L, M>(a, Pw, (int64_t)map_ldg(nt + (int64_t)c * kTileRows + r, a.nslots, a.status) * B + b));
+                    L::acc_add(acc2, leaf_load<L, M>(a, Pw, (int64_t)map_ldg(nt + (int64_t)c * kTileRows + r2, a.nslots, a.status) * B + b));
                 }
                 if (ls >= 0) leaf_store<L, M>(a, (int64_t)ls * B + b, L::result(a.g, node * B + b, a.nB, acc));
                 if (ls2 >= 0) leaf_store<L, M>(a, (int64_t)ls2 * B + b, L::result(a.g, node2 * B + b, a.nB, acc2));
+            }
+        }
+    }
+}
+
+// The F32C leaf gather on packed fp32 pairs (B a power of two >= 32, Q in column pairs):
+// the lane layout of k_niv_gather_h2, Sum2 over the double-word copies of both columns
+// at once, then g(x) minus the sum in double-word arithmetic (LeafF32C::result on both
+// halves), written back as one 16-byte group. Bit-identical to k_mob_leaf_b.
+template <bool NARROW>
+__global__ void __launch_bounds__(kGatherThreads, 2) k_mob_leaf_h2(MobArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int half = lane >> 4, cp = lane & 15;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    ulonglong2 *__restrict__ Q = reinterpret_cast<ulonglong2 *>(a.Q);   // one per column pair
+    const int64_t B = a.B, B2 = a.B / 2;
+    const uint32_t B2u = (uint32_t)(a.B / 2);
+    const float *g = reinterpret_cast<const float *>(a.g);
+    for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
+        const int32_t *rl = a.row_leaf + tile * kTileRows;
+        if (__all_sync(0xffffffffu, rl[lane] < 0)) continue;   // no leaf row in this tile
+        const int k = a.tile_k[tile];
+        const int32_t *__restrict__ nt = a.Nt + a.tile_off[tile];
+        for (int r0 = 0; r0 < 8; ++r0) {
+            const int ra = r0 + 16 * half, rb = ra + 8;
+            const int32_t la = chk(rl[ra], -1, a.nslots, -1, a.status), lb = chk(rl[rb], -1, a.nslots, -1, a.status);
+            if (la < 0 && lb < 0) continue;                     // the whole half-warp agrees
+            const int64_t na = chk(a.row_node[tile * kTileRows + ra], -1, a.nB / a.B, 0, a.status);
+            const int64_t nb = chk(a.row_node[tile * kTileRows + rb], -1, a.nB / a.B, 0, a.status);
+            for (int64_t bp = cp; bp < B2; bp += 16) {
+                const ulonglong2 *__restrict__ Qb = Q + bp;
+                Acc2 x{0ull, 0ull}, y{0ull, 0ull};
+                int c = 0;
+                for (; c + 8 <= k; c += 8) {
+                    int32_t sa[8], sb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        sa[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + ra, a.nslots, a.status);
+                        sb[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + rb, a.nslots, a.status);
+                    }
+                    ulonglong2 va[8], vb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        va[u] = __ldg(NARROW ? Qb + (uint32_t)sa[u] * B2u : Qb + (int64_t)sa[u] * B2);
+                        vb[u] = __ldg(NARROW ? Qb + (uint32_t)sb[u] * B2u : Qb + (int64_t)sb[u] * B2);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        acc2_add(x, va[u].x, va[u].y);
+                        acc2_add(y, vb[u].x, vb[u].y);
+                    }
+                }
+                for (; c < k; ++c) {
+                    const ulonglong2 va = __ldg(Qb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + ra, a.nslots, a.status) * B2);
+                    const ulonglong2 vb = __ldg(Qb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + rb, a.nslots, a.status) * B2);
+                    acc2_add(x, va.x, va.y);
+                    acc2_add(y, vb.x, vb.y);
+                }
+                f32x2 sh, sl;
+                ulonglong2 r;
+                if (la >= 0) {
+                    two_sum2(x.s, x.e, sh, sl);
+                    const int64_t i = na * B + 2 * bp;
+                    dw_add2(*reinterpret_cast<const f32x2 *>(g + i), *reinterpret_cast<const f32x2 *>(g + a.nB + i),
+                            f2_neg(sh), f2_neg(sl), r.x, r.y);
+                    Q[(int64_t)la * B2 + bp] = r;
+                }
+                if (lb >= 0) {
+                    two_sum2(y.s, y.e, sh, sl);
+                    const int64_t i = nb * B + 2 * bp;
+                    dw_add2(*reinterpret_cast<const f32x2 *>(g + i), *reinterpret_cast<const f32x2 *>(g + a.nB + i),
+                            f2_neg(sh), f2_neg(sl), r.x, r.y);
+                    Q[(int64_t)lb * B2 + bp] = r;
+                }
             }
         }
     }
@@ -972,16 +1348,16 @@ __global__ void __launch_bounds__(kGatherThreads, 3) k_mob_leaf_b(MobArgs a) {
 template <class M, bool DWQ>
 __global__ void k_mob_diff(const int32_t *__restrict__ slot_node, int64_t nslots, int32_t B,
                            const unsigned long long *__restrict__ P, const unsigned char *__restrict__ esc,
-                           const float2 *__restrict__ Q, void *f, int64_t nB) {
+                           const float2 *__restrict__ Q, bool pair_q, void *f, int64_t nB, uint32_t *status) {
     const int64_t total = nslots * B;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i / B;
-        const int32_t node = slot_node[s];
+        const int32_t node = chk(slot_node[s], -1, nB / B, -1, status);
         if (node < 0) continue;
         const int64_t bl = i - s * B;
         const int64_t o = (int64_t)node * B + bl;
         if constexpr (DWQ) {
-            const float2 y = Q[i], yp = Q[i - B];
+            const float2 y = dwq_load(Q, i, pair_q), yp = dwq_load(Q, i - B, pair_q);
             const DW r = dw_add({y.x, y.y}, {-yp.x, -yp.y});
             float *q = reinterpret_cast<float *>(f);
             q[o] = r.hi;
@@ -1028,7 +1404,9 @@ ScanShape scan_shape(int64_t nslots, int32_t B) {
 template <class Pol>
 static cudaError_t launch_scan_t(const ScanArgs &a, const ScanShape &sh, cudaStream_t st) {
     dim3 grid((unsigned)sh.ntiles, (unsigned)sh.groups);
-    k_chain_scan<Pol><<<grid, kScanThreads, 0, st>>>(a);
+    ScanArgs args = a;
+    args.pair_words = std::is_same<Pol, PolF32C>::value && f32c_pair_words(a.B);
+    k_chain_scan<Pol><<<grid, kScanThreads, 0, st>>>(args);
     return cudaGetLastError();
 }
 
@@ -1055,8 +1433,13 @@ static cudaError_t launch_gather_t(const GatherArgs &a, int num_sms, cudaStream_
     (narrow ? k_niv_gather_b<Pol, g, true><<<grid, kGatherThreads, 0, st>>>(a)             \
             : k_niv_gather_b<Pol, g, false><<<grid, kGatherThreads, 0, st>>>(a))
         if (G == 32) {               // B a multiple of 32: two columns per lane
-            if (narrow) k_niv_gather_h<Pol, true><<<grid, kGatherThreads, 0, st>>>(a);
-            else k_niv_gather_h<Pol, false><<<grid, kGatherThreads, 0, st>>>(a);
+            if constexpr (std::is_same<Pol, PolF32C>::value) {   // prefixes in column pairs (f32c_pair_words)
+                if (narrow) k_niv_gather_h2<true><<<grid, kGatherThreads, 0, st>>>(a);
+                else k_niv_gather_h2<false><<<grid, kGatherThreads, 0, st>>>(a);
+            } else {
+                if (narrow) k_niv_gather_h<Pol, true><<<grid, kGatherThreads, 0, st>>>(a);
+                else k_niv_gather_h<Pol, false><<<grid, kGatherThreads, 0, st>>>(a);
+            }
             return cudaGetLastError();
         }
         switch (G) {
@@ -1096,6 +1479,13 @@ static cudaError_t launch_leaf_t(const MobArgs &a, int64_t nslots, int num_sms, 
 #define MZ_LEAF_B(g)                                                                     \
     (narrow ? k_mob_leaf_b<L, M, g, true><<<grid, kGatherThreads, 0, st>>>(a)              \
             : k_mob_leaf_b<L, M, g, false><<<grid, kGatherThreads, 0, st>>>(a))
+        if constexpr (M::kDW) {
+            if (a.pair_q) {         // Q in column pairs: the packed compensated gather
+                if (narrow) k_mob_leaf_h2<true><<<grid, kGatherThreads, 0, st>>>(a);
+                else k_mob_leaf_h2<false><<<grid, kGatherThreads, 0, st>>>(a);
+                return cudaGetLastError();
+            }
+        }
         switch (G) {
             case 2: MZ_LEAF_B(2); break;
             case 4: MZ_LEAF_B(4); break;
@@ -1133,7 +1523,16 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     const bool per_thread = pow2 && (int64_t)a.B * nslots < ((int64_t)1 << 31);
     int G = 1;
     const bool lanes = per_thread && a.B == 1 && !anti;   // one function: LR lanes per row
-    if (lanes) {
+    if (lanes && a.lanes == 32 && a.la_width && a.slot_sched && a.mob_ncrit) {
+        threads = 128;
+        G = 32;
+        switch (a.la_width) {
+            case 2: fn = (void *)k_mob_wave_la<M, 2>; break;
+            case 4: fn = (void *)k_mob_wave_la<M, 4>; break;
+            case 8: fn = (void *)k_mob_wave_la<M, 8>; break;
+            default: fn = (void *)k_mob_wave_la<M, 16>; break;
+        }
+    } else if (lanes) {
         threads = 128;
         G = a.lanes;
         switch (G) {
@@ -1162,6 +1561,7 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     }
     MobArgs args = a;
     args.Q = Q;
+    args.pair_q = dwq && f32c_pair_words(a.B);
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
     if (e != cudaSuccess) return e;
@@ -1180,8 +1580,12 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     if (!anti) {
         if ((e = launch_leaf_t<L, M>(args, nslots, num_sms, st)) != cudaSuccess) return e;
         mark_event(++*launches, st);
-        if (dwq) k_mob_diff<M, true><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P, a.esc, Q, a.f, a.nB);
-        else k_mob_diff<M, false><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P, a.esc, nullptr, a.f, a.nB);
+        if (dwq)
+            k_mob_diff<M, true><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P, a.esc, Q, args.pair_q != 0,
+                                                        a.f, a.nB, a.status);
+        else
+            k_mob_diff<M, false><<<eblocks, 256, 0, st>>>(slot_node, nslots, a.B, a.P, a.esc, nullptr, false, a.f,
+                                                         a.nB, a.status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         mark_event(++*launches, st);

@@ -31,7 +31,14 @@ struct ScanArgs {
     uint32_t *status;
     int64_t spin_limit;
     int64_t withhold;        // test hook: tile whose look-back flag is never published (-1: none)
+    int32_t pair_words;      // set by the launcher: F32C prefixes stored in column pairs (f32c_pair_words)
 };
+
+// F32C with B a power of two >= 32: the chain scan stores the prefixes of columns b, b + 1
+// (b even) of a slot as one 16-byte group hi_b, hi_b+1, lo_b, lo_b+1, which the batched
+// gather reads as packed fp32 pairs; the Moebius double-word copies Q are kept the same
+// way for the leaf gather. Other batch sizes keep one (hi, lo) word per column.
+inline bool f32c_pair_words(int64_t B) { return B >= 32 && (B & (B - 1)) == 0; }
 
 struct GatherArgs {
     int32_t blocks_per_sm;    // grid size: resident 256-thread blocks per SM
@@ -45,6 +52,7 @@ struct GatherArgs {
     void *g;
     int64_t nB;
     int64_t nslots;           // rows of P; nslots * B < 2^32 lets the batched gather index in 32 bits
+    uint32_t *status;         // MZ_DEBUG builds: where a failed bounds check is reported
 };
 
 struct MobArgs {
@@ -58,6 +66,7 @@ struct MobArgs {
     const int32_t *mob_level;   // level of each processed row
     int32_t pace_ns;            // sleep per level of distance before polling (0: none)
     int64_t n;                  // rows of the forward substitution's schedule
+    int64_t nslots;             // slots of the prefix array (bound of every map entry)
     int32_t B;
     const void *g;
     void *f;
@@ -80,6 +89,11 @@ struct MobArgs {
     int64_t ntiles;
     int32_t gather_blocks_per_sm;
     int32_t lanes;           // batch 1: lanes per row of the forward substitution (1, 2, 4, 8, 16 or 32)
+    // batch 1, 32 lanes: look-ahead tables (null: no look-ahead)
+    const int32_t *slot_sched;   // [nslots] schedule index of the row in each slot, -1 elsewhere
+    const uint8_t *mob_ncrit;    // [n] trailing entries of each row one level below it
+    int32_t la_width;            // lanes per row segment (2, 4, 8 or 16; 0: no look-ahead)
+    int32_t pair_q;              // set by the launcher: Q in column pairs (F32C, f32c_pair_words)
 };
 
 // Device build (mz_build.cu).
@@ -177,6 +191,12 @@ cudaError_t launch_build_tiles_var(const int32_t *N, int64_t ntiles, const int64
                                    const int32_t *tile_rows, const int64_t *tile_off, int32_t *Nt, int num_sms,
                                    cudaStream_t st);
 cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream_t st);
+// Look-ahead tables of a U-level schedule: slot_sched[s] = schedule index of the row in slot
+// s (-1 elsewhere), ncrit[i] = number of trailing entries of row i whose rows are one level
+// below it (at most 255).
+cudaError_t launch_build_lookahead(const int32_t *Nm, const int64_t *mob_off, const int32_t *mob_kp,
+                                   const int32_t *mob_level, const int32_t *mob_slot, int64_t nmob, int64_t nslots,
+                                   int32_t *slot_sched, uint8_t *ncrit, int num_sms, cudaStream_t st);
 // Marks (slot_ref[s] = 1) every slot that some tile row holds as an entry of another
 // chain: the rows of the forward substitution. slot_ref is zeroed before the launch.
 cudaError_t launch_mark_referenced(const int32_t *Nt, const int64_t *tile_off, const int32_t *tile_k,

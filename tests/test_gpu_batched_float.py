@@ -193,13 +193,14 @@ def test_every_autotune_shape(multi):
     # one function per row: every lane count with every blocks-per-SM choice
     xi1 = to_device(fi[:, :1].copy(), mz.MZ_I64)
     for lanes in autotune.CANDIDATES["mobius_lanes"]:
-        for mb in autotune.CANDIDATES["mobius_blocks_per_sm"]:
-            mz.mz_plan_tune(plan.handle, mobius_lanes=lanes, mobius_blocks_per_sm=mb)
-            gm1 = plan.mobius(xi1).cpu().numpy()
-            plan.check()
-            for i in range(len(ps)):
-                sl = slice(off[i], off[i + 1])
-                assert (gm1[sl, 0] == want_m[i][:, 0]).all(), (lanes, mb, ps[i].name)
+        for la in autotune.CANDIDATES["mobius_lookahead"]:
+            for mb in autotune.CANDIDATES["mobius_blocks_per_sm"]:
+                mz.mz_plan_tune(plan.handle, mobius_lanes=lanes, mobius_lookahead=la, mobius_blocks_per_sm=mb)
+                gm1 = plan.mobius(xi1).cpu().numpy()
+                plan.check()
+                for i in range(len(ps)):
+                    sl = slice(off[i], off[i + 1])
+                    assert (gm1[sl, 0] == want_m[i][:, 0]).all(), (lanes, la, mb, ps[i].name)
     for sh in shapes:
         mz.mz_plan_tune(plan.handle, **sh)
         gz = plan.zeta(xi).cpu().numpy()
@@ -218,3 +219,39 @@ def test_every_autotune_shape(multi):
             sl = slice(off[i], off[i + 1])
             _check_zeta_cols(gv[sl], ff[sl], Zs[i], mz.MZ_F32C, (31,), f"{sh} {p.name}")
             _check_mobius_cols(mv[sl], ff[sl], Zs[i], mus[i], mz.MZ_F32C, (31,), f"{sh} {p.name}")
+
+
+@pytest.mark.parametrize("batch", [32, 64, 128])
+def test_f32c_pair_gathers(multi, batch):
+    """B a power of two >= 32 takes the packed-pair F32C gathers (zeta, and the Moebius leaf
+    gather) over prefixes and double-word copies stored in column pairs, one to four
+    column pairs per lane. Zeta and Moebius of every poset against the oracle on sampled
+    columns; and the Moebius, whose every stage works column by column in a fixed order
+    (no tile shape enters it, unlike the chain scan's), must give each column the bits the
+    same column gets at B = 16, where each word is one (hi, lo) pair and no pair layout is
+    used."""
+    ps, cids, Zs, mus, off = multi
+    plan = mz.Plan.batch([(p.n, p.src, p.dst, c) for p, c in zip(ps, cids)])
+    n = int(off[-1])
+    f = pg.function_values(n, batch, "f32u", 80 + batch)
+    lo = (pg.function_values(n, batch, "f32u", 90 + batch) * np.float32(2.0 ** -30)).astype(np.float32)
+    x = to_device((f, lo), mz.MZ_F32C)
+    g = from_device(plan.zeta(x), mz.MZ_F32C)
+    m = plan.mobius(x)
+    plan.check()
+    exact = f.astype(np.float64) + lo.astype(np.float64)
+    mv = from_device(m, mz.MZ_F32C)
+    cols = (0, 17, batch - 1)
+    for i, p in enumerate(ps):
+        sl = slice(off[i], off[i + 1])
+        for b in cols:
+            ex = exact[sl, b]
+            assert_close(g[sl, b], oracle.zeta(Zs[i], ex), oracle.zeta(Zs[i], np.abs(ex)), mz.MZ_F32C,
+                         f"B={batch} {p.name} zeta col {b}")
+            res = oracle.zeta(Zs[i], mv[sl, b]) - ex
+            assert_close(res, np.zeros_like(res), oracle.zeta(Zs[i], np.abs(mv[sl, b])) + np.abs(ex), mz.MZ_F32C,
+                         f"B={batch} {p.name} mobius residual col {b}")
+    for s in range(0, batch, 16):
+        ms = plan.mobius(to_device((f[:, s:s + 16].copy(), lo[:, s:s + 16].copy()), mz.MZ_F32C))
+        plan.check()
+        assert torch.equal(m[:, :, s:s + 16].contiguous().view(torch.int32), ms.view(torch.int32)), s

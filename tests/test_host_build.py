@@ -1,6 +1,7 @@
 """CPU tests of the C ABI's host side: the library loads and exports every
 declared symbol, and the host build (order, chains, niv map, levels, errors)
 agrees with the oracle. Plans here are built host-only: no GPU is touched."""
+import ctypes
 import os
 import re
 from math import comb
@@ -30,9 +31,39 @@ def test_library_exports_every_declared_symbol():
     assert mz.LIBRARY_PATH.endswith("libmz.so")
 
 
+def header_struct(name):
+    """(field, C type) of the typedef struct `name` in mz.h, in order."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "mz.h")).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        m = re.match(r"(.*?)\s*\(\s*\*\s*(\w+)\s*\)\s*\(.*\)$", decl)      # function pointer
+        if m:
+            fields.append((m.group(2), "ptr"))
+            continue
+        m = re.match(r"(.*?)(\**)\s*(\w+)$", decl)
+        fields.append((m.group(3), "ptr" if m.group(2) else m.group(1).strip()))
+    return fields
+
+
+@pytest.mark.parametrize("cname,cls", [("mz_build_opts", "_Opts"), ("mz_plan_info_t", "PlanInfo"),
+                                       ("mz_tuning", "Tuning")])
+def test_binding_structs_mirror_the_header(cname, cls):
+    """The binding's ctypes structures have the header's fields, in order, with the same
+    types, so that the library and the binding agree on every offset."""
+    ctype = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "ptr": ctypes.c_void_p}
+    want = [(f, ctype[t]) for f, t in header_struct(cname)]
+    got = list(getattr(mz, cls)._fields_)
+    assert got == want
+
+
 def test_status_strings():
     for code, name in enumerate(["MZ_OK", "MZ_ERR_INVALID_ARG", "MZ_ERR_CYCLE", "MZ_ERR_BAD_CHAINS", "MZ_ERR_OOM",
-                                 "MZ_ERR_CUDA", "MZ_ERR_TIMEOUT", "MZ_ERR_UNSUPPORTED", "MZ_ERR_NO_DEVICE"]):
+                                 "MZ_ERR_CUDA", "MZ_ERR_TIMEOUT", "MZ_ERR_UNSUPPORTED", "MZ_ERR_NO_DEVICE",
+                                 "MZ_ERR_BOUNDS"]):
         assert mz.lib.mz_status_string(code).decode() == name
 
 
