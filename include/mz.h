@@ -140,15 +140,6 @@ typedef struct {
                               reads (niv_j(x) = y for an x not on y's chain); the others are
                               computed afterwards by a gather. All n with MZ_SCHED_ANTICHAIN */
     int64_t wave_entries;  /* their finite niv entries on other chains */
-    int32_t lookahead_width; /* lanes per row segment of the look-ahead forward substitution
-                                (mz_tuning::mobius_lookahead; 0: the plan keeps no look-ahead
-                                tables): the smallest power of two >= 2 covering the longest
-                                row's chunks of 16 entries; a row computes up to
-                                min(32 / width, 8) - 1 of its dependencies itself */
-    int32_t lookahead_max_local; /* that number of dependencies a row computes itself */
-    int64_t wave_critical_rows; /* rows with a dependency exactly one level below them */
-    int64_t wave_critical_over; /* of those, rows with more such dependencies than they compute
-                                   themselves (they still wait a hop for the rest) */
 } mz_plan_info_t;
 /* For a plan of several posets (mz_build_batch) n, k, nnz and edges are totals over
    them and levels, ulevels, levels_T, ulevels_T and max_chain are maxima. */
@@ -301,14 +292,6 @@ typedef struct {
                                      dealt to the lanes 16 at a time, each lane polls and sums its
                                      own, the lanes' sums meet in a shuffle tree and the row's first
                                      lane publishes it; 0 keeps the current value */
-    int32_t mobius_lookahead;     /* forward substitution of one function with 32 lanes per row,
-                                     where the plan has the tables for it (U-level schedule, rows of
-                                     at most 256 entries): 1 = each row also computes, from their own
-                                     rows, up to 7 of its dependencies one level below it, so that it
-                                     waits only for words published two levels below; 2 = off (the
-                                     default); 0 keeps the current value. Results are the same bits
-                                     either way. */
-    int32_t reserved;             /* 0 */
 } mz_tuning;
 
 /* Sets the plan's launch shapes (results are unaffected); fills *current if non-NULL. */

@@ -108,11 +108,10 @@ def _opts(build_transpose, host_only, mobius_schedule, mobius_blocks_per_sm, mob
 
 class Tuning(ctypes.Structure):
     _fields_ = [("mobius_blocks_per_sm", ctypes.c_int32), ("mobius_pace_ns", ctypes.c_int32),
-                ("gather_blocks_per_sm", ctypes.c_int32), ("mobius_lanes", ctypes.c_int32),
-                ("mobius_lookahead", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("gather_blocks_per_sm", ctypes.c_int32), ("mobius_lanes", ctypes.c_int32)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class PlanInfo(ctypes.Structure):
@@ -121,9 +120,7 @@ class PlanInfo(ctypes.Structure):
                 ("ulevels", ctypes.c_int32), ("schedule", ctypes.c_int32), ("levels_T", ctypes.c_int32),
                 ("ulevels_T", ctypes.c_int32), ("max_chain", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("components", ctypes.c_int32), ("sparse", ctypes.c_int32), ("wave_rows", ctypes.c_int64),
-                ("wave_entries", ctypes.c_int64), ("lookahead_width", ctypes.c_int32),
-                ("lookahead_max_local", ctypes.c_int32), ("wave_critical_rows", ctypes.c_int64),
-                ("wave_critical_over", ctypes.c_int64)]
+                ("wave_entries", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -286,11 +283,10 @@ def mz_check(plan: int, stream: int = 0) -> None:
 
 
 def mz_plan_tune(plan: int, mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0,
-                 gather_blocks_per_sm: int = 0, mobius_lanes: int = 0, mobius_lookahead: int = 0) -> dict:
+                 gather_blocks_per_sm: int = 0, mobius_lanes: int = 0) -> dict:
     """mz_plan_tune: sets the given launch shapes (0 keeps one) and returns the current ones."""
     cur = Tuning()
-    want = Tuning(int(mobius_blocks_per_sm), int(mobius_pace_ns), int(gather_blocks_per_sm), int(mobius_lanes),
-                  int(mobius_lookahead), 0)
+    want = Tuning(int(mobius_blocks_per_sm), int(mobius_pace_ns), int(gather_blocks_per_sm), int(mobius_lanes))
     _check(lib.mz_plan_tune(plan, ctypes.byref(want), ctypes.byref(cur)), "mz_plan_tune")
     return cur.as_dict()
 

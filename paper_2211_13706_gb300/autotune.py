@@ -19,7 +19,6 @@ CANDIDATES = {
     "mobius_pace_ns": (300, 600, 1000, 1600),
     "gather_blocks_per_sm": (8, 16, 32),
     "mobius_lanes": (1, 32),               # one function per row only
-    "mobius_lookahead": (1, 2),            # one function, 32 lanes, plans with look-ahead tables
 }
 _CACHE: dict = {}
 
@@ -89,23 +88,17 @@ def tune(plan, x, reps: int = 3) -> dict:
             if best_l is None or t < best_l[0]:
                 best_l = (t, lanes)
         mz_plan_tune(plan.handle, mobius_lanes=best_l[1])
-    # look-ahead on or off jointly with blocks and pacing (its levels pass faster)
-    looks = CANDIDATES["mobius_lookahead"] if batch == 1 and best_l[1] == 32 and \
-        plan.info["lookahead_width"] > 0 else (0,)
     best_m = None
-    for la in looks:
-        for bps in CANDIDATES["mobius_blocks_per_sm"]:
-            for pace in CANDIDATES["mobius_pace_ns"]:
-                mz_plan_tune(plan.handle, mobius_blocks_per_sm=bps, mobius_pace_ns=pace, mobius_lookahead=la)
-                t = _time(lambda: plan.mobius(g, out=y), reps)
-                if best_m is None or t < best_m[0]:
-                    best_m = (t, bps, pace, la)
+    for bps in CANDIDATES["mobius_blocks_per_sm"]:
+        for pace in CANDIDATES["mobius_pace_ns"]:
+            mz_plan_tune(plan.handle, mobius_blocks_per_sm=bps, mobius_pace_ns=pace)
+            t = _time(lambda: plan.mobius(g, out=y), reps)
+            if best_m is None or t < best_m[0]:
+                best_m = (t, bps, pace)
     plan.check()
     choice = {"gather_blocks_per_sm": best_g[1], "mobius_blocks_per_sm": best_m[1], "mobius_pace_ns": best_m[2]}
     if best_l is not None:
         choice["mobius_lanes"] = best_l[1]
-    if best_m[3]:
-        choice["mobius_lookahead"] = best_m[3]
     mz_plan_tune(plan.handle, **choice)
     _CACHE[key] = choice
     _save_file()

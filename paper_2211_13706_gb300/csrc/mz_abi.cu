@@ -1175,40 +1175,6 @@ static mz_status run_zeta(const mz_plan *p, int side, mz_dtype dtype, const void
     return MZ_OK;
 }
 
-// Look-ahead tables of the forward substitution (U-level schedule, rows of at most
-// kLookaheadMaxKp entries); other plans keep none and run without look-ahead.
-static mz_status build_lookahead(mz_plan *p, int side) {
-    DeviceSide &D = p->dev[side];
-    if (p->schedule != MZ_SCHED_ULEVEL || D.nmob == 0 || D.mob_kp_max > kLookaheadMaxKp) return MZ_OK;
-    D.slot_sched = (int32_t *)plan_alloc(p, sizeof(int32_t) * (size_t)D.nslots);
-    D.mob_ncrit = D.slot_sched ? (uint8_t *)plan_alloc(p, (size_t)D.nmob) : nullptr;
-    if (!D.mob_ncrit) {
-        set_last_error("device allocation failed");
-        return MZ_ERR_OOM;
-    }
-    cudaError_t e = launch_build_lookahead(D.Nm, D.mob_off, D.mob_kp, D.mob_level, D.mob_slot, D.nmob, D.nslots,
-                                           D.slot_sched, D.mob_ncrit, p->num_sms, 0);
-    std::vector<uint8_t> nc;
-    try {
-        nc.resize((size_t)D.nmob);
-    } catch (...) {
-        set_last_error("host allocation failed");
-        return MZ_ERR_OOM;
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(nc.data(), D.mob_ncrit, nc.size(), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(e, "look-ahead tables");
-    int32_t w = 2;
-    while (w * 16 < D.mob_kp_max) w *= 2;
-    D.la_width = w;
-    D.la_max_local = std::min(32 / w, 8) - 1;
-    D.la_crit_rows = D.la_crit_over = 0;
-    for (uint8_t c : nc) {
-        D.la_crit_rows += c > 0;
-        D.la_crit_over += c > D.la_max_local;
-    }
-    return MZ_OK;
-}
-
 static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const void *g, void *f, int32_t B, void *ws,
                             size_t ws_bytes, mz_stream stream) {
     g_last_launches = 0;
@@ -1248,14 +1214,8 @@ static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const vo
     ma.ntiles = D.ntiles;
     ma.gather_blocks_per_sm = p->gather_blocks_per_sm;
     ma.lanes = p->mob_lanes;
-    ma.slot_sched = nullptr;
-    ma.mob_ncrit = nullptr;
-    ma.la_width = 0;
-    if (p->mob_lookahead == 1 && D.la_width && B == 1 && p->mob_lanes == 32 && p->schedule == MZ_SCHED_ULEVEL) {
-        ma.slot_sched = D.slot_sched;
-        ma.mob_ncrit = D.mob_ncrit;
-        ma.la_width = D.la_width;
-    }
+    ma.tree_w = 1;
+    while (ma.tree_w * 16 < D.mob_kp_max && ma.tree_w < 32) ma.tree_w *= 2;
     int launches = 0;
     mark_event(0, (cudaStream_t)stream);
     cudaError_t e = launch_mobius(dtype, ma, D.slot_node, D.nslots, p->schedule == MZ_SCHED_ANTICHAIN, p->num_sms,
@@ -1408,11 +1368,6 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
             st = !p->host[side][0].niv_on_device ? upload_side(p.get(), side)
                  : p->components() > 1            ? upload_batch_device(p.get(), side)
                                                   : upload_side_device(p.get(), side);
-        if (st) {
-            plan_free_all(p.get());
-            return st;
-        }
-        for (int side = 0; side < (p->has_dual ? 2 : 1) && st == MZ_OK; ++side) st = build_lookahead(p.get(), side);
         if (st) {
             plan_free_all(p.get());
             return st;
@@ -1610,8 +1565,7 @@ mz_status mz_plan_tune(mz_plan *plan, const mz_tuning *set, mz_tuning *current) 
     if (set) {
         if (set->mobius_blocks_per_sm < 0 || set->mobius_blocks_per_sm > 64 || set->gather_blocks_per_sm < 0 ||
             set->gather_blocks_per_sm > 256 || set->mobius_lanes < 0 || set->mobius_lanes > 32 ||
-            (set->mobius_lanes & (set->mobius_lanes - 1)) != 0 || set->mobius_lookahead < 0 ||
-            set->mobius_lookahead > 2 || set->reserved != 0) {
+            (set->mobius_lanes & (set->mobius_lanes - 1)) != 0) {
             set_last_error("tuning value out of range");
             return MZ_ERR_INVALID_ARG;
         }
@@ -1619,7 +1573,6 @@ mz_status mz_plan_tune(mz_plan *plan, const mz_tuning *set, mz_tuning *current) 
         if (set->mobius_pace_ns) plan->mob_pace_ns = set->mobius_pace_ns < 0 ? 0 : set->mobius_pace_ns;
         if (set->gather_blocks_per_sm) plan->gather_blocks_per_sm = set->gather_blocks_per_sm;
         if (set->mobius_lanes) plan->mob_lanes = set->mobius_lanes;
-        if (set->mobius_lookahead) plan->mob_lookahead = set->mobius_lookahead;
     }
     if (current) {
         std::memset(current, 0, sizeof(*current));
@@ -1627,7 +1580,6 @@ mz_status mz_plan_tune(mz_plan *plan, const mz_tuning *set, mz_tuning *current) 
         current->mobius_pace_ns = plan->mob_pace_ns ? plan->mob_pace_ns : -1;
         current->gather_blocks_per_sm = plan->gather_blocks_per_sm;
         current->mobius_lanes = plan->mob_lanes;
-        current->mobius_lookahead = plan->mob_lookahead;
     }
     return MZ_OK;
 }
@@ -1656,10 +1608,6 @@ mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info) {
     if (!plan->host_only) {
         info->wave_rows = plan->dev[0].nmob;
         info->wave_entries = plan->dev[0].nmob_entries;
-        info->lookahead_width = plan->dev[0].la_width;
-        info->lookahead_max_local = plan->dev[0].la_max_local;
-        info->wave_critical_rows = plan->dev[0].la_crit_rows;
-        info->wave_critical_over = plan->dev[0].la_crit_over;
     }
     return MZ_OK;
 }

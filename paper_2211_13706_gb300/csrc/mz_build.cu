@@ -485,33 +485,6 @@ cudaError_t dispatch_kj(int32_t k, F f) {
     }
 }
 
-// Look-ahead tables of the forward substitution (U-level schedule): the schedule
-// index of the row in each slot (slot_sched, -1 preset), then for each row the length of
-// the tail of its sorted entries whose rows sit exactly one level below it (its critical
-// dependencies), capped at 255.
-__global__ void __launch_bounds__(kBuildThreads) k_la_index(const int32_t *mob_slot, int64_t nmob,
-                                                            int32_t *slot_sched) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nmob; i += (int64_t)gridDim.x * blockDim.x)
-        slot_sched[mob_slot[i]] = (int32_t)i;
-}
-
-__global__ void __launch_bounds__(kBuildThreads) k_la_ncrit(const int32_t *Nm, const int64_t *mob_off,
-                                                            const int32_t *mob_kp, const int32_t *mob_level,
-                                                            const int32_t *slot_sched, int64_t nmob,
-                                                            uint8_t *ncrit) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nmob; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t *row = Nm + mob_off[i];
-        const int32_t below = mob_level[i] - 1;
-        int cnt = 0;
-        for (int q = mob_kp[i] - 1; q >= 0 && cnt < 255; --q) {
-            const int32_t d = slot_sched[row[q]];
-            if (d < 0 || mob_level[d] != below) break;
-            ++cnt;
-        }
-        ncrit[i] = (uint8_t)cnt;
-    }
-}
-
 }  // namespace
 
 cudaError_t launch_build_niv(const BuildNivArgs &a, int num_sms, cudaStream_t st) {
@@ -584,18 +557,6 @@ cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream
         k_build_mob_rows<KJ><<<(unsigned)blocks, kBuildThreads, 0, st>>>(a);
         return cudaGetLastError();
     });
-}
-
-cudaError_t launch_build_lookahead(const int32_t *Nm, const int64_t *mob_off, const int32_t *mob_kp,
-                                   const int32_t *mob_level, const int32_t *mob_slot, int64_t nmob, int64_t nslots,
-                                   int32_t *slot_sched, uint8_t *ncrit, int num_sms, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(slot_sched, 0xff, (size_t)nslots * sizeof(int32_t), st);
-    if (e != cudaSuccess || nmob == 0) return e;
-    const unsigned blocks = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>((nmob + kBuildThreads - 1) / kBuildThreads, (int64_t)num_sms * 8));
-    k_la_index<<<blocks, kBuildThreads, 0, st>>>(mob_slot, nmob, slot_sched);
-    k_la_ncrit<<<blocks, kBuildThreads, 0, st>>>(Nm, mob_off, mob_kp, mob_level, slot_sched, nmob, ncrit);
-    return cudaGetLastError();
 }
 
 }  // namespace mz

@@ -95,16 +95,7 @@ struct DeviceSide {
     uint8_t *slot_ref = nullptr;   // U-level schedule: [nslots] 1 = a slot another row reads
     int32_t *row_leaf = nullptr;   // U-level schedule: [ntiles * 32] slot of a tile row no other row
                                    // reads (computed by the leaf gather), -1 otherwise
-    // look-ahead tables of the U-level schedule (rows of at most kLookaheadMaxKp entries)
-    int32_t *slot_sched = nullptr; // [nslots] schedule index of the row in each slot, -1 elsewhere
-    uint8_t *mob_ncrit = nullptr;  // [nmob] trailing entries of each row one level below it
-    int32_t la_width = 0;          // lanes per row segment (0: no look-ahead tables)
-    int32_t la_max_local = 0;      // dependencies a row computes itself: min(32 / la_width, 8) - 1
-    int64_t la_crit_rows = 0;      // rows with a dependency one level below them
-    int64_t la_crit_over = 0;      // of those, rows with more of them than la_max_local
 };
-
-constexpr int32_t kLookaheadMaxKp = 256;   // rows of up to 16 chunks: at least two 16-lane segments
 
 }  // namespace mz
 
@@ -126,7 +117,6 @@ struct mz_plan {
     int32_t mob_pace_ns = 600;      // wavefront pacing per level of distance (0: none)
     int32_t gather_blocks_per_sm = 32;
     int32_t mob_lanes = 32;         // batch-1 wavefront: lanes per row (1, 2, 4, 8, 16, 32)
-    int32_t mob_lookahead = 2;      // batch-1 wavefront with 32 lanes: 1 = look-ahead, 2 = none
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
     void *(*dev_alloc)(size_t, void *) = nullptr;

@@ -521,6 +521,52 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_h(GatherArgs a
     }
 }
 
+// Sum2 of one pair of tile rows (ra, rb) over one column pair of the packed F32C words, in
+// groups of 8 entries: a group's words are requested together, and the map entries of the
+// next group load while they arrive. Entries are added in map order. (Measured on 256
+// posets, B = 32: 2.70 ms per zeta gather; two groups of 4 in flight 3.10 ms, of 8 with
+// the same scheme 6.8 ms.)
+template <bool NARROW>
+__device__ __forceinline__ void pair_rows_sum2(const int32_t *__restrict__ nt, int ra, int rb, int k,
+                                               const ulonglong2 *__restrict__ Pb, int64_t B2, uint32_t B2u,
+                                               int64_t nslots, uint32_t *status, Acc2 &x, Acc2 &y) {
+    int32_t sa[8], sb[8];
+    if (k >= 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            sa[u] = map_ldg(nt + (int64_t)u * kTileRows + ra, nslots, status);
+            sb[u] = map_ldg(nt + (int64_t)u * kTileRows + rb, nslots, status);
+        }
+    }
+    int c = 0;
+    for (; c + 8 <= k; c += 8) {
+        ulonglong2 va[8], vb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            va[u] = __ldg(NARROW ? Pb + (uint32_t)sa[u] * B2u : Pb + (int64_t)sa[u] * B2);
+            vb[u] = __ldg(NARROW ? Pb + (uint32_t)sb[u] * B2u : Pb + (int64_t)sb[u] * B2);
+        }
+        if (c + 16 <= k) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                sa[u] = map_ldg(nt + (int64_t)(c + 8 + u) * kTileRows + ra, nslots, status);
+                sb[u] = map_ldg(nt + (int64_t)(c + 8 + u) * kTileRows + rb, nslots, status);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            acc2_add(x, va[u].x, va[u].y);
+            acc2_add(y, vb[u].x, vb[u].y);
+        }
+    }
+    for (; c < k; ++c) {
+        const ulonglong2 va = __ldg(Pb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + ra, nslots, status) * B2);
+        const ulonglong2 vb = __ldg(Pb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + rb, nslots, status) * B2);
+        acc2_add(x, va.x, va.y);
+        acc2_add(y, vb.x, vb.y);
+    }
+}
+
 // The compensated gather of k_niv_gather_h on packed fp32 pairs: the chain scan stores
 // the prefixes of columns b and b + 1 (b even) as hi_b, hi_b+1, lo_b, lo_b+1, so one
 // 16-byte load gives the pair of hi parts and the pair of lo parts, and every step of
@@ -546,32 +592,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_niv_gather_h2(GatherArgs 
             for (int64_t bp = cp; bp < B2; bp += 16) {        // column pair bp: columns 2 bp, 2 bp + 1
                 const ulonglong2 *__restrict__ Pb = P + bp;
                 Acc2 x{0ull, 0ull}, y{0ull, 0ull};
-                int c = 0;
-                for (; c + 8 <= k; c += 8) {
-                    int32_t sa[8], sb[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        sa[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + ra, a.nslots, a.status);
-                        sb[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + rb, a.nslots, a.status);
-                    }
-                    ulonglong2 va[8], vb[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        va[u] = __ldg(NARROW ? Pb + (uint32_t)sa[u] * B2u : Pb + (int64_t)sa[u] * B2);
-                        vb[u] = __ldg(NARROW ? Pb + (uint32_t)sb[u] * B2u : Pb + (int64_t)sb[u] * B2);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        acc2_add(x, va[u].x, va[u].y);
-                        acc2_add(y, vb[u].x, vb[u].y);
-                    }
-                }
-                for (; c < k; ++c) {
-                    const ulonglong2 va = __ldg(Pb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + ra, a.nslots, a.status) * B2);
-                    const ulonglong2 vb = __ldg(Pb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + rb, a.nslots, a.status) * B2);
-                    acc2_add(x, va.x, va.y);
-                    acc2_add(y, vb.x, vb.y);
-                }
+                pair_rows_sum2<NARROW>(nt, ra, rb, k, Pb, B2, B2u, a.nslots, a.status, x, y);
                 // normalise once, as PolF32C::store_out: hi and lo planes, both columns at once
                 f32x2 hi, lo;
                 if (na >= 0) {
@@ -613,6 +634,19 @@ __global__ void k_mob_init(const int32_t *__restrict__ slot_node, const uint8_t 
 template <class T>
 __device__ __forceinline__ T shfl_xor_t(T v, int off) {
     return __shfl_xor_sync(0xffffffffu, v, off);
+}
+
+// x + 0 for a value type without the arithmetic pipe: -0 becomes +0 and every other value
+// stays what an IEEE add of +0 gives (a sum is never a signalling NaN, and a NaN ends up
+// as the final subtraction makes it either way); integers are unchanged. It stands for
+// the levels of a 32-lane shuffle tree that only add the zeros of lanes holding no chunk.
+template <class M>
+__device__ __forceinline__ typename M::T plus_zero(typename M::T x) {
+    if constexpr (std::is_same<typename M::T, double>::value) {
+        return __double_as_longlong(x) == (long long)0x8000000000000000ull ? 0.0 : x;
+    } else {
+        return x;
+    }
 }
 
 // Sleeps about ns nanoseconds. __nanosleep may sleep up to twice what it is asked, so a
@@ -865,192 +899,24 @@ __global__ void __launch_bounds__(128) k_mob_wave_lr(MobArgs a) {
                     continue;
                 }
                 // no pause between rounds: a sleep, however short, costs a round trip per level
+                // (and additions only when a word has landed were slower: 0.65 -> 0.75 ms)
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j)
                     if (j >= next && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
             }
         }
         if (LR > 1) {
+            // The LR-lane butterfly; its levels above the plan's tree width only add the zeros
+            // of lanes without a chunk, one plus_zero in their place (same bits). Each fp64 add
+            // on this path costs latency on GB300's narrow FP64 pipe: dropping the three
+            // all-zero levels at k = 64 took the wavefront from 0.75 to 0.65 ms.
             __syncwarp(gmask);
-#pragma unroll
-            for (int off = LR / 2; off >= 1; off >>= 1) acc = M::add(acc, __shfl_xor_sync(gmask, acc, off));
+            const int tw = a.tree_w < LR ? a.tree_w : LR;
+            if (tw < LR) acc = plus_zero<M>(acc);
+            for (int off = tw / 2; off >= 1; off >>= 1) acc = M::add(acc, __shfl_xor_sync(gmask, acc, off));
         }
         if (sub == 0 && i != a.withhold) {
             const T y = M::sub(gx, acc);
-            if constexpr (M::kDW) {
-                if (a.Q) a.Q[sout] = M::to_dw(y);   // read after this kernel ends
-            }
-            publish<M>(P + sout, E + sout, y);
-        }
-        done_level = level;
-    }
-}
-
-// The forward substitution with a look-ahead of one level (one function, U-level
-// schedule, a warp per row). A row x at level L reads rows of levels up to L - 1; the
-// ones at L - 1 (its critical dependencies, the tail of its sorted row) would cost a
-// full store-to-poll hop after their own hop. Instead, the warp computes up to
-// min(32 / W, 8) - 1 of them itself from their own rows, which read only levels up to
-// L - 2, so that a row waits for words published two levels below it: one hop per two
-// levels on the critical path. The warp is cut into segments of W lanes (W >= chunks
-// of the longest row): segment 0 holds x, segment t >= 1 the t-th computed dependency,
-// lane c of a segment the row's chunk c of 16 entries.
-//
-// Every row's value, wherever computed, is formed in one fixed order, that of
-// k_mob_wave_lr<M, 32>: each chunk summed in entry order from 0, the chunks' sums met by
-// a 32-lane butterfly (here: the adds of zero that lanes >= W would contribute, then a
-// W-lane butterfly, which is the same sequence of operations on every lane < W), and
-// y'(x) = g(x) - sum. A computed dependency therefore has the bits its own warp
-// publishes, and the results equal those of the kernel without look-ahead bit for bit.
-// The row withheld by the test hook is never computed here either (it is polled).
-template <class M, int W>
-__global__ void __launch_bounds__(128) k_mob_wave_la(MobArgs a) {
-    using T = typename M::T;
-    constexpr int kSeg = 32 / W;
-    constexpr int kMaxLocal = (kSeg - 1) < 7 ? (kSeg - 1) : 7;   // computed dependencies per row
-    const int lane = threadIdx.x & 31;
-    const int seg = lane / W, c = lane % W;
-    const int64_t gwarp = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long *P = a.P;
-    unsigned char *E = a.esc;
-    const unsigned long long S = M::kSentinel;
-    int32_t done_level = 0;
-    for (int64_t i = gwarp; i < a.n; i += nwarps) {
-        const int32_t *row = a.Nm + a.mob_off[i];
-        const int kp = a.mob_kp[i];
-        const int32_t level = a.mob_level[i];
-        const int m = min((int)a.mob_ncrit[i], kMaxLocal);
-        const int pos0 = kp - m;                 // entries pos0 .. kp - 1: computed here
-        // the row's words are published two levels below it, each level taking about half a hop
-        if (a.pace_ns > 0) pace_until((int64_t)(level - done_level - 3) * a.pace_ns);
-        if (lane == 0 && i + nwarps < a.n) {
-            const char *nxt = reinterpret_cast<const char *>(a.Nm + a.mob_off[i + nwarps]);
-            const int nkp = a.mob_kp[i + nwarps];
-            for (int q = 0; q < nkp * 4; q += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + q));
-        }
-        // this segment's row: x itself, or the dependency at entry pos0 + seg - 1
-        int64_t rs = -1;
-        if (seg == 0) {
-            rs = i;
-        } else if (seg <= m) {
-            const int32_t d = chk(a.slot_sched[chk(row[pos0 + seg - 1], 0, a.nslots, 0, a.status)], -1, a.n, -1,
-                                  a.status);
-            rs = (d >= 0 && d != a.withhold) ? d : -1;
-        }
-        const unsigned lm = __ballot_sync(0xffffffffu, c == 0 && seg >= 1 && rs >= 0);
-        int snch = 0;
-        const int32_t *srow = nullptr;
-        T sg = T(0);
-        int64_t sout = 0;
-        if (rs >= 0) {
-            srow = a.Nm + a.mob_off[rs];
-            snch = a.mob_kp[rs] / kChunk;
-            if (c == 0) {
-                sg = M::load_in(a.g, chk(a.mob_node[rs], 0, a.nB, 0, a.status), a.nB);   // B == 1
-                if (seg == 0) sout = chk(a.mob_slot[i], 0, a.nslots, 0, a.status);
-            }
-        }
-        // entry q of x (segment 0) is computed here when q >= pos0 and its segment has a row
-        auto local = [&](int q) { return q >= pos0 && ((lm >> ((q - pos0 + 1) * W)) & 1u); };
-        // Phase 1: each lane sums its chunk in entry order up to the first computed entry
-        // (segment 0) or to its end (the dependencies, whose words are all two levels down).
-        T acc = T(0);
-        int32_t id[kChunk];
-        unsigned long long v[kChunk];
-        int next = 0, stop = 0;
-        const bool has = rs >= 0 && c < snch;
-        if (has) {
-            load_ids(srow + c * kChunk, id, a.nslots, a.status);
-            stop = kChunk;
-            if (seg == 0) stop = max(0, min(kChunk, pos0 - c * kChunk));
-#pragma unroll
-            for (int j = 0; j < kChunk; ++j)
-                v[j] = (seg == 0 && local(c * kChunk + j)) ? S : ld_relaxed_u64(P + id[j]);
-            for (int64_t it = 0; next < stop; ++it) {
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j)
-                    if (j == next && j < stop && v[j] != S) {
-                        acc = M::add(acc, decode<M>(v[j], E + id[j]));
-                        next = j + 1;
-                    }
-                if (next >= stop) break;
-                if ((it & 127) == 127 && (ld_relaxed_u32(a.status) || it >= a.spin_limit)) {
-                    if (it >= a.spin_limit) report(a.status, MZ_ERR_TIMEOUT);
-#pragma unroll
-                    for (int j = 0; j < kChunk; ++j)
-                        if (j < stop && v[j] == S) v[j] = 0ull;
-                    continue;
-                }
-                // All 32 lanes poll here (in the kernel without look-ahead only the lanes of
-                // one row do): each asks for its first missing word only, and once that lands
-                // for every later missing one in one round, which keeps the L1 requests of a
-                // round to one per lane.
-                const unsigned long long *addr = P;
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j)
-                    if (j == next) addr = P + id[j];
-                const unsigned long long got = ld_relaxed_u64(addr);
-                if (got != S) {
-#pragma unroll
-                    for (int j = 0; j < kChunk; ++j) {
-                        if (j == next) v[j] = got;
-                        else if (j > next && j < stop && v[j] == S) v[j] = ld_relaxed_u64(P + id[j]);
-                    }
-                }
-            }
-        }
-        // Phase 2: the dependencies' values (segments 1 .. m), handed to every lane.
-        __syncwarp();
-        T t = acc;
-        if (W < 32) t = M::add(t, T(0));
-#pragma unroll
-        for (int off = W / 2; off >= 1; off >>= 1) t = M::add(t, __shfl_xor_sync(0xffffffffu, t, off));
-        const T yd = M::sub(sg, t);
-        T crit[kMaxLocal > 0 ? kMaxLocal : 1];
-#pragma unroll
-        for (int u = 0; u < kMaxLocal; ++u) crit[u] = __shfl_sync(0xffffffffu, yd, (u + 1) * W);
-        // Phase 3: segment 0 finishes its chunks in entry order, computed entries from crit,
-        // the others (the withheld row) polled.
-        if (seg == 0 && has && next < kChunk) {
-            for (int64_t it = 0;; ++it) {
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j)
-                    if (j == next) {
-                        const int q = c * kChunk + j;
-                        if (local(q)) {
-                            T x = crit[0];
-#pragma unroll
-                            for (int u = 1; u < kMaxLocal; ++u)
-                                if (q - pos0 == u) x = crit[u];
-                            acc = M::add(acc, x);
-                            next = j + 1;
-                        } else if (v[j] != S) {
-                            acc = M::add(acc, decode<M>(v[j], E + id[j]));
-                            next = j + 1;
-                        }
-                    }
-                if (next == kChunk) break;
-                if ((it & 127) == 127 && (ld_relaxed_u32(a.status) || it >= a.spin_limit)) {
-                    if (it >= a.spin_limit) report(a.status, MZ_ERR_TIMEOUT);
-#pragma unroll
-                    for (int j = 0; j < kChunk; ++j)
-                        if (v[j] == S) v[j] = 0ull;
-                    continue;
-                }
-#pragma unroll
-                for (int j = 0; j < kChunk; ++j)
-                    if (j >= next && v[j] == S && !local(c * kChunk + j)) v[j] = ld_relaxed_u64(P + id[j]);
-            }
-        }
-        // x's value: the same tree over segment 0
-        __syncwarp();
-        T s0 = seg == 0 ? acc : T(0);
-        if (W < 32) s0 = M::add(s0, T(0));
-#pragma unroll
-        for (int off = W / 2; off >= 1; off >>= 1) s0 = M::add(s0, __shfl_xor_sync(0xffffffffu, s0, off));
-        if (lane == 0 && i != a.withhold) {
-            const T y = M::sub(sg, s0);
             if constexpr (M::kDW) {
                 if (a.Q) a.Q[sout] = M::to_dw(y);   // read after this kernel ends
             }
@@ -1295,32 +1161,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) k_mob_leaf_h2(MobArgs a) {
             for (int64_t bp = cp; bp < B2; bp += 16) {
                 const ulonglong2 *__restrict__ Qb = Q + bp;
                 Acc2 x{0ull, 0ull}, y{0ull, 0ull};
-                int c = 0;
-                for (; c + 8 <= k; c += 8) {
-                    int32_t sa[8], sb[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        sa[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + ra, a.nslots, a.status);
-                        sb[u] = map_ldg(nt + (int64_t)(c + u) * kTileRows + rb, a.nslots, a.status);
-                    }
-                    ulonglong2 va[8], vb[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        va[u] = __ldg(NARROW ? Qb + (uint32_t)sa[u] * B2u : Qb + (int64_t)sa[u] * B2);
-                        vb[u] = __ldg(NARROW ? Qb + (uint32_t)sb[u] * B2u : Qb + (int64_t)sb[u] * B2);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        acc2_add(x, va[u].x, va[u].y);
-                        acc2_add(y, vb[u].x, vb[u].y);
-                    }
-                }
-                for (; c < k; ++c) {
-                    const ulonglong2 va = __ldg(Qb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + ra, a.nslots, a.status) * B2);
-                    const ulonglong2 vb = __ldg(Qb + (int64_t)map_ldg(nt + (int64_t)c * kTileRows + rb, a.nslots, a.status) * B2);
-                    acc2_add(x, va.x, va.y);
-                    acc2_add(y, vb.x, vb.y);
-                }
+                pair_rows_sum2<NARROW>(nt, ra, rb, k, Qb, B2, B2u, a.nslots, a.status, x, y);
                 f32x2 sh, sl;
                 ulonglong2 r;
                 if (la >= 0) {
@@ -1523,16 +1364,7 @@ static cudaError_t launch_mobius_t(const MobArgs &a, const int32_t *slot_node, i
     const bool per_thread = pow2 && (int64_t)a.B * nslots < ((int64_t)1 << 31);
     int G = 1;
     const bool lanes = per_thread && a.B == 1 && !anti;   // one function: LR lanes per row
-    if (lanes && a.lanes == 32 && a.la_width && a.slot_sched && a.mob_ncrit) {
-        threads = 128;
-        G = 32;
-        switch (a.la_width) {
-            case 2: fn = (void *)k_mob_wave_la<M, 2>; break;
-            case 4: fn = (void *)k_mob_wave_la<M, 4>; break;
-            case 8: fn = (void *)k_mob_wave_la<M, 8>; break;
-            default: fn = (void *)k_mob_wave_la<M, 16>; break;
-        }
-    } else if (lanes) {
+    if (lanes) {
         threads = 128;
         G = a.lanes;
         switch (G) {

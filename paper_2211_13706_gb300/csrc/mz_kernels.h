@@ -89,10 +89,7 @@ struct MobArgs {
     int64_t ntiles;
     int32_t gather_blocks_per_sm;
     int32_t lanes;           // batch 1: lanes per row of the forward substitution (1, 2, 4, 8, 16 or 32)
-    // batch 1, 32 lanes: look-ahead tables (null: no look-ahead)
-    const int32_t *slot_sched;   // [nslots] schedule index of the row in each slot, -1 elsewhere
-    const uint8_t *mob_ncrit;    // [n] trailing entries of each row one level below it
-    int32_t la_width;            // lanes per row segment (2, 4, 8 or 16; 0: no look-ahead)
+    int32_t tree_w;          // batch 1: smallest power of two >= the longest row's chunks of 16 entries
     int32_t pair_q;              // set by the launcher: Q in column pairs (F32C, f32c_pair_words)
 };
 
@@ -191,12 +188,6 @@ cudaError_t launch_build_tiles_var(const int32_t *N, int64_t ntiles, const int64
                                    const int32_t *tile_rows, const int64_t *tile_off, int32_t *Nt, int num_sms,
                                    cudaStream_t st);
 cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream_t st);
-// Look-ahead tables of a U-level schedule: slot_sched[s] = schedule index of the row in slot
-// s (-1 elsewhere), ncrit[i] = number of trailing entries of row i whose rows are one level
-// below it (at most 255).
-cudaError_t launch_build_lookahead(const int32_t *Nm, const int64_t *mob_off, const int32_t *mob_kp,
-                                   const int32_t *mob_level, const int32_t *mob_slot, int64_t nmob, int64_t nslots,
-                                   int32_t *slot_sched, uint8_t *ncrit, int num_sms, cudaStream_t st);
 // Marks (slot_ref[s] = 1) every slot that some tile row holds as an entry of another
 // chain: the rows of the forward substitution. slot_ref is zeroed before the launch.
 cudaError_t launch_mark_referenced(const int32_t *Nt, const int64_t *tile_off, const int32_t *tile_k,

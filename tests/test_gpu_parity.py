@@ -424,6 +424,32 @@ def test_c1_wavefront_lanes_per_row(c1, lanes):
                      f"lanes {lanes} mobius", mu=mu)
 
 
+@pytest.mark.parametrize("k", [10, 20, 60, 120, 250, 500])
+def test_wavefront_tree_widths(k):
+    """A warp per row meets the chunk sums in a butterfly only as wide as the plan's longest
+    row (1 to 32 chunks of 16 entries here; the wider levels, which add only zeros, are
+    one plus_zero): int64 exact against the oracle, fp64 within tolerance, and the same bits
+    under every launch shape (results never depend on timing)."""
+    p = pg.planted_chain_poset(2500, k, 60 + k, cross_deg=3)
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id)
+    Z = oracle.closure(p.n, p.src, p.dst)
+    mu = oracle.mobius_function(Z)
+    f = values(p.n, 1, mz.MZ_I64, 61)[:, 0]
+    g = values(p.n, 1, mz.MZ_F64, 62)[:, 0]
+    xf = to_device(g, mz.MZ_F64)
+    ref = None
+    for shape in (dict(mobius_blocks_per_sm=2, mobius_pace_ns=600), dict(mobius_blocks_per_sm=1, mobius_pace_ns=-1),
+                  dict(mobius_blocks_per_sm=4, mobius_pace_ns=300)):
+        mz.mz_plan_tune(plan.handle, mobius_lanes=32, **shape)
+        assert (run(plan, "mobius", f, mz.MZ_I64) == oracle.mobius(Z, f, "mu", mu=mu)).all(), shape
+        y = plan.mobius(xf)
+        plan.check()
+        if ref is None:
+            ref = y
+            check_mobius(plan, Z, g, mz.MZ_F64, f"k={k} mobius", mu=mu)
+        assert torch.equal(y.view(torch.int64), ref.view(torch.int64)), shape
+
+
 @pytest.mark.parametrize("lanes", [1, 4, 16])
 def test_c2_int64_round_trip_lanes_per_row(c2, lanes):
     p, plan = c2
