@@ -116,7 +116,12 @@ typedef struct {
        MZ_ERR_UNSUPPORTED). mz_build_batch builds all its posets in one dataflow launch
        when every one of them keeps a dense map (else MZ_ERR_UNSUPPORTED). Not with
        host_only (MZ_ERR_INVALID_ARG). A bounded wait that runs out fails the build with
-       MZ_ERR_TIMEOUT. */
+       MZ_ERR_TIMEOUT. 2: as 1, and for a single poset given without chains (chain_id
+       NULL) Alg. 1's maximum matching runs on the device too (a greedy maximal matching,
+       then phases of augmenting paths, each found by a breadth-first search from every
+       free node at once). Its chains come from another maximum matching than the host's:
+       the same number k of chains, but the plan may then differ from the host build's.
+       Other values: MZ_ERR_INVALID_ARG. */
     int32_t device_build;
 } mz_build_opts;
 

@@ -183,7 +183,7 @@ def _check(st: int, where: str):
 def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, host_only: bool = False,
              mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0,
              mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0, niv_format: int = 0,
-             device_build: bool = False, torch_allocator: bool = False) -> int:
+             device_build: int = 0, torch_allocator: bool = False) -> int:
     """mz_build: returns the plan handle (an integer). Host arrays are int32.
     torch_allocator: the plan's device memory (and the build's scratch) comes from
     PyTorch's caching allocator through the dev_alloc / dev_free callbacks."""
@@ -204,7 +204,7 @@ def mz_build(n: int, src, dst, chain_id=None, *, build_transpose: bool = False, 
 def mz_build_batch(posets, *, build_transpose: bool = False, host_only: bool = False,
                    mobius_schedule: int = MZ_SCHED_ULEVEL, spin_limit: int = 0, debug_withhold: int = 0,
                    mobius_blocks_per_sm: int = 0, mobius_pace_ns: int = 0, niv_format: int = 0,
-                   device_build: bool = False, torch_allocator: bool = False) -> int:
+                   device_build: int = 0, torch_allocator: bool = False) -> int:
     """mz_build_batch: `posets` is a list of (n, src, dst, chain_id or None)."""
     count = len(posets)
     ns = np.array([int(p[0]) for p in posets], dtype=np.int64)

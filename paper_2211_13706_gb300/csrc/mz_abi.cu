@@ -364,6 +364,101 @@ class BuildScratch {
     std::vector<void *> bufs_;
 };
 
+// Alg. 1's maximum matching on the device (mz_build_opts::device_build = 2, no chains
+// given): next[u] = the node matched below u, or -1. The kernels of mz_build.cu do the
+// work; the host only sequences the launches and reads the counters between levels.
+// The result is checked on the host (every matched pair is an edge, no node matched
+// twice) before it is used.
+static mz_status device_matching(mz_plan *p, int64_t n, const std::vector<int64_t> &ptr,
+                                 const std::vector<int32_t> &adj, std::vector<int32_t> &next, std::string &err) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        err = std::string("device matching: ") + cudaGetErrorString(e);
+        return MZ_ERR_CUDA;
+    }
+    BuildScratch tmp(p);
+    int64_t *d_ptr;
+    int32_t *d_adj;
+    mz_status st;
+    if ((st = tmp.put(&d_ptr, ptr.data(), ptr.size())) || (st = tmp.put(&d_adj, adj.data(), adj.size()))) {
+        err = "device matching: " + std::string(mz_last_error());
+        return st;
+    }
+    int32_t *mu = tmp.get<int32_t>(n), *mv = tmp.get<int32_t>(n), *parent = tmp.get<int32_t>(n);
+    int32_t *root = tmp.get<int32_t>(n), *fa = tmp.get<int32_t>(n), *fb = tmp.get<int32_t>(n);
+    int32_t *ends = tmp.get<int32_t>(n);
+    uint32_t *done = tmp.get<uint32_t>(n), *flags = tmp.get<uint32_t>(4);
+    unsigned long long *counts = tmp.get<unsigned long long>(4);
+    if (!mu || !mv || !parent || !root || !fa || !fb || !ends || !done || !flags || !counts) {
+        err = "device allocation failed";
+        return MZ_ERR_OOM;
+    }
+    auto fail = [&](cudaError_t ce, const char *what) {
+        err = std::string("device matching: ") + what + ": " + cudaGetErrorString(ce);
+        return MZ_ERR_CUDA;
+    };
+    const size_t nb = sizeof(int32_t) * (size_t)n;
+    if ((e = cudaMemset(mu, 0xff, nb)) != cudaSuccess || (e = cudaMemset(mv, 0xff, nb)) != cudaSuccess ||
+        (e = cudaMemset(flags, 0, 16)) != cudaSuccess)
+        return fail(e, "cudaMemset");
+    // greedy start: rounds until no free upper node wins a free child (bounded)
+    for (int round = 0; round < 64; ++round) {
+        uint32_t changed = 0;
+        if ((e = cudaMemset(flags, 0, 4)) != cudaSuccess) return fail(e, "cudaMemset");
+        if ((e = launch_match_greedy(d_ptr, d_adj, n, mu, mv, flags, sms, 0)) != cudaSuccess)
+            return fail(e, "greedy launch");
+        if ((e = cudaMemcpy(&changed, flags, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e, "cudaMemcpy");
+        if (!changed) break;
+    }
+    // phases of augmenting paths; each flips at least one path, so at most n phases
+    for (int64_t phase = 0; phase <= n; ++phase) {
+        if ((e = cudaMemset(parent, 0xff, nb)) != cudaSuccess || (e = cudaMemset(done, 0, nb)) != cudaSuccess ||
+            (e = cudaMemset(counts, 0, 32)) != cudaSuccess)
+            return fail(e, "cudaMemset");
+        if ((e = launch_match_roots(d_ptr, n, mu, root, fa, counts, sms, 0)) != cudaSuccess)
+            return fail(e, "roots launch");
+        unsigned long long c[4];
+        if ((e = cudaMemcpy(c, counts, 32, cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e, "cudaMemcpy");
+        int64_t fcount = (int64_t)c[0];
+        int32_t *cur = fa, *nxt = fb;
+        while (fcount > 0) {                 // one launch per level of the search forest
+            if ((e = cudaMemset(counts + 1, 0, 8)) != cudaSuccess) return fail(e, "cudaMemset");
+            if ((e = launch_match_expand(d_ptr, d_adj, cur, fcount, nxt, counts + 1, mu, mv, parent, root, done, ends,
+                                         counts + 2, sms, 0)) != cudaSuccess)
+                return fail(e, "search launch");
+            if ((e = cudaMemcpy(c, counts, 32, cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return fail(e, "cudaMemcpy");
+            fcount = (int64_t)c[1];
+            std::swap(cur, nxt);
+        }
+        const int64_t found = (int64_t)c[2];
+        if (found == 0) break;               // no augmenting path: the matching is maximum
+        if ((e = launch_match_augment(ends, found, n, parent, mu, mv, flags + 1, sms, 0)) != cudaSuccess)
+            return fail(e, "augment launch");
+    }
+    uint32_t status = 0;
+    if ((e = cudaMemcpy(&status, flags + 1, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e, "cudaMemcpy");
+    next.assign((size_t)n, -1);
+    if ((e = cudaMemcpy(next.data(), mu, nb, cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e, "cudaMemcpy");
+    // check: a matching of edges
+    std::vector<char> below((size_t)n, 0);
+    for (int64_t u = 0; u < n && status == 0; ++u) {
+        const int32_t v = next[(size_t)u];
+        if (v < 0) continue;
+        if (v >= n || below[(size_t)v] || !std::binary_search(adj.begin() + ptr[u], adj.begin() + ptr[u + 1], v))
+            status = MZ_ERR_CUDA;
+        else
+            below[(size_t)v] = 1;
+    }
+    if (status) {
+        err = "device matching produced an invalid matching";
+        return MZ_ERR_CUDA;
+    }
+    return MZ_OK;
+}
+
 // The same layouts as upload_side for a single poset whose niv map is built on the
 // device (mz_build_opts::device_build): the host sends the children lists and the
 // slot layout, the kernels of mz_build.cu build the map, the U levels, the tiles and
@@ -1229,7 +1324,15 @@ static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const vo
 // the offsets of the union.
 static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, const int64_t *m,
                                   const int32_t *const *src, const int32_t *const *dst,
-                                  const int32_t *const *chain_id, bool dual, int niv_format, bool device_niv) {
+                                  const int32_t *const *chain_id, bool dual, int niv_format, bool device_niv,
+                                  bool device_chains) {
+    // Alg. 1 on the device for a single poset given without chains (device_build = 2)
+    Matcher matcher;
+    if (device_chains && count == 1)
+        matcher = [p](int64_t nn, const std::vector<int64_t> &ptr, const std::vector<int32_t> &adj,
+                      std::vector<int32_t> &next, std::string &err) {
+            return device_matching(p, nn, ptr, adj, next, err);
+        };
     p->host[0].resize(count);
     if (dual) p->host[1].resize(count);
     std::vector<mz_status> sts(count, MZ_OK);
@@ -1238,7 +1341,8 @@ static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, c
         try {
             std::vector<int32_t> s(src[c], src[c] + m[c]), d(dst[c], dst[c] + m[c]);
             const int32_t *cid = chain_id ? chain_id[c] : nullptr;
-            sts[c] = build_host_side(n[c], s, d, cid, niv_format, device_niv, p->host[0][c], errs[c]);
+            sts[c] = build_host_side(n[c], s, d, cid, niv_format, device_niv, p->host[0][c], errs[c],
+                                     matcher ? &matcher : nullptr);
             if (sts[c] == MZ_OK && dual) {
                 // the dual poset: every edge flipped, the same chains (a chain of P is a chain of its dual)
                 sts[c] = build_host_side(n[c], d, s, p->host[0][c].chain_id.data(), niv_format, device_niv,
@@ -1333,8 +1437,12 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
         return MZ_ERR_INVALID_ARG;
     }
 
+    if (o.device_build < 0 || o.device_build > 2) {
+        set_last_error("device_build is 0, 1 or 2");
+        return MZ_ERR_INVALID_ARG;
+    }
     mz_status st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0, o.niv_format,
-                                    o.device_build != 0);
+                                    o.device_build != 0, o.device_build == 2);
     if (st) return st;
     if (o.device_build && count > 1)
         for (int side = 0; side < (p->has_dual ? 2 : 1); ++side)

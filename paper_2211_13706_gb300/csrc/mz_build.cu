@@ -485,6 +485,95 @@ cudaError_t dispatch_kj(int32_t k, F f) {
     }
 }
 
+// ---- Alg. 1 on the device: a maximum matching between the edge sources ("upper" copies)
+// and edge targets ("lower" copies) of the nodes, for a minimum path cover. A greedy
+// maximal matching first, then phases of augmenting paths: a breadth-first search over
+// alternating paths from every free upper node at once (one launch per level; each lower
+// node is claimed by one search tree, and each tree augments along the first free lower
+// node it reaches), then every found path is flipped. A phase that finds no path ends it:
+// the trees then covered every alternating path from a free upper node (Berge's theorem).
+// match_u[u] = lower node matched to u (-1 free), match_v[v] = upper node matched to v.
+
+// Each free upper node takes its first free child, if it wins the claim.
+__global__ void __launch_bounds__(kBuildThreads) k_match_greedy(const int64_t *ptr, const int32_t *adj, int64_t n,
+                                                                int32_t *match_u, int32_t *match_v,
+                                                                uint32_t *changed) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        if (match_u[u] >= 0) continue;
+        for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e) {
+            const int32_t v = adj[e];
+            if (match_v[v] < 0 && atomicCAS(&match_v[v], -1, (int32_t)u) == -1) {
+                match_u[u] = v;
+                *changed = 1u;
+                break;
+            }
+        }
+    }
+}
+
+// The roots of a phase: every free upper node with a child.
+__global__ void __launch_bounds__(kBuildThreads) k_match_roots(const int64_t *ptr, int64_t n, const int32_t *match_u,
+                                                               int32_t *root, int32_t *frontier,
+                                                               unsigned long long *count) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        if (match_u[u] < 0 && ptr[u + 1] > ptr[u]) {
+            root[u] = (int32_t)u;
+            frontier[atomicAdd(count, 1ull)] = (int32_t)u;
+        }
+}
+
+// One level: each upper node of the frontier tries its children over unmatched edges. A
+// child claimed first here (parent_v) is either free (the tree's path ends there, once per
+// tree) or leads on to its mate, which joins the next frontier in the same tree.
+__global__ void __launch_bounds__(kBuildThreads) k_match_expand(const int64_t *ptr, const int32_t *adj,
+                                                                const int32_t *frontier, int64_t fcount,
+                                                                int32_t *next, unsigned long long *ncount,
+                                                                const int32_t *match_u, const int32_t *match_v,
+                                                                int32_t *parent_v, int32_t *root,
+                                                                uint32_t *root_done, int32_t *ends,
+                                                                unsigned long long *ecount) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = frontier[i];
+        const int32_t r = root[u];
+        if (ld_relaxed(&root_done[r])) continue;
+        for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e) {
+            const int32_t v = adj[e];
+            if (v == match_u[u]) continue;
+            if (atomicCAS(&parent_v[v], -1, u) != -1) continue;
+            const int32_t w = match_v[v];
+            if (w < 0) {
+                if (atomicCAS(&root_done[r], 0u, 1u) == 0u) ends[atomicAdd(ecount, 1ull)] = v;
+                break;
+            }
+            root[w] = r;
+            next[atomicAdd(ncount, 1ull)] = w;
+        }
+    }
+}
+
+// Flips each found path, from its free lower end up to its root: every upper node on it
+// takes the lower node below it on the path. The paths share no node. A walk longer than
+// n steps (impossible for a path of a tree) stops and reports MZ_ERR_TIMEOUT.
+__global__ void __launch_bounds__(kBuildThreads) k_match_augment(const int32_t *ends, int64_t ecount, int64_t n,
+                                                                 const int32_t *parent_v, int32_t *match_u,
+                                                                 int32_t *match_v, uint32_t *status) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ecount; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = ends[i];
+        for (int64_t step = 0;; ++step) {
+            if (step > n) {
+                atomicCAS(status, 0u, (uint32_t)MZ_ERR_TIMEOUT);
+                break;
+            }
+            const int32_t u = parent_v[v];
+            const int32_t prev = match_u[u];
+            match_u[u] = v;
+            match_v[v] = u;
+            if (prev < 0) break;   // u is the root
+            v = prev;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_build_niv(const BuildNivArgs &a, int num_sms, cudaStream_t st) {
@@ -514,6 +603,11 @@ cudaError_t launch_build_tiles(const int32_t *N, int64_t n, int32_t k, int32_t *
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms * 8));
     k_build_tiles<<<(unsigned)blocks, kBuildThreads, 0, st>>>(N, n, k, ntiles, Nt);
     return cudaGetLastError();
+}
+
+// Blocks of one thread per item, at most 16 resident blocks per SM (grid-stride loops).
+static int64_t grid_for(int64_t items, int num_sms) {
+    return std::max<int64_t>(1, std::min<int64_t>((items + kBuildThreads - 1) / kBuildThreads, (int64_t)num_sms * 16));
 }
 
 static int64_t warp_blocks(int64_t items, int num_sms) {
@@ -557,6 +651,35 @@ cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream
         k_build_mob_rows<KJ><<<(unsigned)blocks, kBuildThreads, 0, st>>>(a);
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_match_greedy(const int64_t *ptr, const int32_t *adj, int64_t n, int32_t *match_u,
+                                int32_t *match_v, uint32_t *changed, int num_sms, cudaStream_t st) {
+    k_match_greedy<<<(unsigned)grid_for(n, num_sms), kBuildThreads, 0, st>>>(ptr, adj, n, match_u, match_v, changed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_roots(const int64_t *ptr, int64_t n, const int32_t *match_u, int32_t *root,
+                               int32_t *frontier, unsigned long long *count, int num_sms, cudaStream_t st) {
+    k_match_roots<<<(unsigned)grid_for(n, num_sms), kBuildThreads, 0, st>>>(ptr, n, match_u, root, frontier, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_expand(const int64_t *ptr, const int32_t *adj, const int32_t *frontier, int64_t fcount,
+                                int32_t *next, unsigned long long *ncount, const int32_t *match_u,
+                                const int32_t *match_v, int32_t *parent_v, int32_t *root, uint32_t *root_done,
+                                int32_t *ends, unsigned long long *ecount, int num_sms, cudaStream_t st) {
+    k_match_expand<<<(unsigned)grid_for(fcount, num_sms), kBuildThreads, 0, st>>>(
+        ptr, adj, frontier, fcount, next, ncount, match_u, match_v, parent_v, root, root_done, ends, ecount);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_augment(const int32_t *ends, int64_t ecount, int64_t n, const int32_t *parent_v,
+                                 int32_t *match_u, int32_t *match_v, uint32_t *status, int num_sms,
+                                 cudaStream_t st) {
+    k_match_augment<<<(unsigned)grid_for(ecount, num_sms), kBuildThreads, 0, st>>>(ends, ecount, n, parent_v,
+                                                                                    match_u, match_v, status);
+    return cudaGetLastError();
 }
 
 }  // namespace mz

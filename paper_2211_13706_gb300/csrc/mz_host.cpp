@@ -178,7 +178,8 @@ std::vector<int32_t> max_matching(int64_t n, const std::vector<int64_t> &ptr, co
 void set_host_threads_cap(int cap) { t_threads_cap = cap; }
 
 mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const std::vector<int32_t> &dst_in,
-                          const int32_t *chain_in, int niv_format, bool device_niv, HostSide &H, std::string &err) {
+                          const int32_t *chain_in, int niv_format, bool device_niv, HostSide &H, std::string &err,
+                          const Matcher *matcher) {
     H = HostSide();
     H.n = n;
     const int64_t m = (int64_t)src_in.size();
@@ -262,7 +263,13 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src_in, const s
         // members in topological order, reversed (bottom first)
         for (int64_t i = n - 1; i >= 0; --i) chains[H.chain_id[H.topo[i]]].push_back(H.topo[i]);
     } else {
-        std::vector<int32_t> next = max_matching(n, ptr, adj);
+        std::vector<int32_t> next;
+        if (matcher) {
+            const mz_status st = (*matcher)(n, ptr, adj, next, err);
+            if (st) return st;
+        } else {
+            next = max_matching(n, ptr, adj);
+        }
         std::vector<char> has_pred(n, 0);
         for (int64_t u = 0; u < n; ++u)
             if (next[u] >= 0) has_pred[next[u]] = 1;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -134,8 +135,15 @@ namespace mz {
 // the niv map (Thm. 4) and both level structures. chain_in may be null.
 // niv_format: 0 = dense unless k > kDenseMaxChains, 1 = dense, 2 = sparse.
 // device_niv: stop after the slot layout and the heights (the device build does the rest).
+// matcher: computes Alg. 1's matching when chain_in is null (null: the host's).
+// A maximum matching of Alg. 1's bipartite graph over the children lists (ptr, adj):
+// next[u] = the node matched below u, or -1.
+using Matcher = std::function<mz_status(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int32_t> &adj,
+                                        std::vector<int32_t> &next, std::string &err)>;
+
 mz_status build_host_side(int64_t n, const std::vector<int32_t> &src, const std::vector<int32_t> &dst,
-                          const int32_t *chain_in, int niv_format, bool device_niv, HostSide &H, std::string &err);
+                          const int32_t *chain_in, int niv_format, bool device_niv, HostSide &H, std::string &err,
+                          const Matcher *matcher = nullptr);
 
 void set_last_error(const std::string &s);
 

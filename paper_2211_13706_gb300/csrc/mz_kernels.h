@@ -188,6 +188,18 @@ cudaError_t launch_build_tiles_var(const int32_t *N, int64_t ntiles, const int64
                                    const int32_t *tile_rows, const int64_t *tile_off, int32_t *Nt, int num_sms,
                                    cudaStream_t st);
 cudaError_t launch_build_mob_rows(const BuildMobArgs &a, int num_sms, cudaStream_t st);
+// Alg. 1 on the device (maximum matching for a minimum path cover), see mz_build.cu.
+cudaError_t launch_match_greedy(const int64_t *ptr, const int32_t *adj, int64_t n, int32_t *match_u,
+                                int32_t *match_v, uint32_t *changed, int num_sms, cudaStream_t st);
+cudaError_t launch_match_roots(const int64_t *ptr, int64_t n, const int32_t *match_u, int32_t *root,
+                               int32_t *frontier, unsigned long long *count, int num_sms, cudaStream_t st);
+cudaError_t launch_match_expand(const int64_t *ptr, const int32_t *adj, const int32_t *frontier, int64_t fcount,
+                                int32_t *next, unsigned long long *ncount, const int32_t *match_u,
+                                const int32_t *match_v, int32_t *parent_v, int32_t *root, uint32_t *root_done,
+                                int32_t *ends, unsigned long long *ecount, int num_sms, cudaStream_t st);
+cudaError_t launch_match_augment(const int32_t *ends, int64_t ecount, int64_t n, const int32_t *parent_v,
+                                 int32_t *match_u, int32_t *match_v, uint32_t *status, int num_sms,
+                                 cudaStream_t st);
 // Marks (slot_ref[s] = 1) every slot that some tile row holds as an entry of another
 // chain: the rows of the forward substitution. slot_ref is zeroed before the launch.
 cudaError_t launch_mark_referenced(const int32_t *Nt, const int64_t *tile_off, const int32_t *tile_k,

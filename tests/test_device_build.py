@@ -20,6 +20,10 @@ def test_device_build_argument_checks():
     with pytest.raises(mz.MzError) as e:
         mz.mz_build(3, [0, 1], [1, 2], device_build=True, host_only=True)
     assert e.value.status == mz.MZ_ERR_INVALID_ARG
+    for bad in (3, -1):
+        with pytest.raises(mz.MzError) as e:
+            mz.mz_build(3, [0, 1], [1, 2], device_build=bad)
+        assert e.value.status == mz.MZ_ERR_INVALID_ARG
     p = pg.paper_example()
     # several posets on the device: dense maps only (a 600-chain antichain keeps a sparse map)
     q600 = pg.antichain_poset(600)
@@ -257,3 +261,78 @@ def test_batch_device_build_names_the_poset_of_a_bad_chain():
     with pytest.raises(mz.MzError) as e:
         mz.Plan.batch(posets, device_build=True)
     assert e.value.status == mz.MZ_ERR_BAD_CHAINS and "poset 4" in str(e.value)
+
+
+# ----------------------------------------------------------------------------- Alg. 1 on the device
+
+def _matching_cases():
+    pl = pg.planted_chain_poset(4096, 16, 1, cross_p=4 / 4096)
+    return [("paper_example", pg.paper_example()), ("boolean_lattice_8", pg.boolean_lattice(8)),
+            ("divisor_lattice_720", pg.divisor_lattice(720)[0]), ("chain_500", pg.chain_poset(500, 1)),
+            ("antichain_100", pg.antichain_poset(100)), ("planted_4096_k16", pl),
+            ("er_400_deg3", pg.er_dag(400, 3, 9)), ("tiny_dag", pg.random_dag_tiny(40, 0.2, 5)),
+            ("er_20000_deg6", pg.er_dag(20000, 6, 3)), ("er_20000_deg2", pg.er_dag(20000, 2, 4))]
+
+
+MATCHING_CASES = _matching_cases()
+
+
+def _assert_path_cover(p, plan):
+    """Every chain of the plan is a path of edges: consecutive members joined by an edge
+    from the upper one to the lower one (u -> v means v <= u)."""
+    cid = plan.export(mz.MZ_EXPORT_CHAIN_ID)
+    pos = plan.export(mz.MZ_EXPORT_CHAIN_POS)
+    edges = set(zip(np.asarray(p.src).tolist(), np.asarray(p.dst).tolist()))
+    order = np.lexsort((pos, cid))
+    c, q = cid[order], pos[order]
+    assert (q[np.r_[True, c[1:] != c[:-1]]] == 0).all()            # each chain starts at position 0
+    for a, b in zip(order[:-1], order[1:]):
+        if cid[a] == cid[b]:
+            assert pos[b] == pos[a] + 1 and (int(b), int(a)) in edges, (int(a), int(b))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,p", MATCHING_CASES, ids=[c[0] for c in MATCHING_CASES])
+def test_device_matching_gives_a_minimum_path_cover(name, p):
+    """device_build = 2: Alg. 1's matching on the device. The chains are a path cover with as
+    many chains as the host's maximum matching gives (both are maximum), and the int64
+    transforms of the plan equal those of the host-chained plan (and the oracle's)."""
+    import torch
+    host = mz.Plan(p.n, p.src, p.dst, None, build_transpose=True)
+    dev = mz.Plan(p.n, p.src, p.dst, None, build_transpose=True, device_build=2)
+    assert dev.info["k"] == host.info["k"], (dev.info["k"], host.info["k"])
+    _assert_path_cover(p, dev)
+    f = pg.function_values(p.n, 1, "i64:1000", 5)[:, 0]
+    x = torch.from_numpy(f).cuda()
+    for op in ("zeta", "mobius", "zeta_T", "mobius_T"):
+        a, b = getattr(host, op)(x), getattr(dev, op)(x)
+        host.check()
+        dev.check()
+        assert torch.equal(a, b), op
+    if p.n <= 4096:
+        Z = oracle.closure(p.n, p.src, p.dst)
+        assert np.array_equal(dev.zeta(x).cpu().numpy(), oracle.zeta(Z, f))
+
+
+@pytest.mark.gpu
+def test_device_matching_er_paper_scale():
+    """The paper's ER DAG at n = 2^20, average degree 4, chains by the device's matching:
+    the host's number of chains, a path cover, and int64 transforms equal to the host plan's."""
+    import torch
+    p = pg.er_dag(1 << 20, 4, 1)
+    host = mz.Plan(p.n, p.src, p.dst, None, device_build=True)
+    dev = mz.Plan(p.n, p.src, p.dst, None, device_build=2)
+    assert dev.info["k"] == host.info["k"]
+    cid = dev.export(mz.MZ_EXPORT_CHAIN_ID)
+    pos = dev.export(mz.MZ_EXPORT_CHAIN_POS)
+    order = np.lexsort((pos, cid))
+    same = cid[order][1:] == cid[order][:-1]
+    lo, hi = order[:-1][same], order[1:][same]                      # consecutive members: hi directly above lo
+    key = lambda a, b: a.astype(np.int64) * p.n + b
+    assert np.isin(key(hi, lo), key(np.asarray(p.src), np.asarray(p.dst))).all()
+    x = torch.from_numpy(pg.function_values(p.n, 1, "i64:1000", 6)[:, 0]).cuda()
+    for op in ("zeta", "mobius"):
+        a, b = getattr(host, op)(x), getattr(dev, op)(x)
+        host.check()
+        dev.check()
+        assert torch.equal(a, b), op
