@@ -102,10 +102,19 @@ def time_single(mz, torch, wl: str, dtype_key: str, steps: int = 10, seed: int =
     tz, tm = e[0].elapsed_time(e[1]) / steps, e[1].elapsed_time(e[2]) / steps
     info = plan.info
     plan.close()
-    return {"workload": WORKLOADS[wl]["desc"], "dtype": dtype_key, "n": p.n, "k": info["k"],
-            "nnz": info["nnz"], "ulevels": info["ulevels"], "sparse_map": bool(info["sparse"]),
-            "host_build_s": round(build_s, 2), "zeta_ms": round(tz, 4), "mobius_ms": round(tm, 4),
-            "value": round(2 * p.n / ((tz + tm) / 1e3), 1), "unit": UNIT}
+    out = {"workload": WORKLOADS[wl]["desc"], "dtype": dtype_key, "n": p.n, "k": info["k"],
+           "nnz": info["nnz"], "ulevels": info["ulevels"], "sparse_map": bool(info["sparse"]),
+           "host_build_s": round(build_s, 2), "zeta_ms": round(tz, 4), "mobius_ms": round(tm, 4),
+           "value": round(2 * p.n / ((tz + tm) / 1e3), 1), "unit": UNIT}
+    if p.chain_id is None:
+        # the same poset built on the device, Alg. 1's matching included (another maximum
+        # matching: the same number of chains)
+        t0 = time.perf_counter()
+        pd = mz.Plan(p.n, p.src, p.dst, None, device_build=2)
+        out["device_build_s"] = round(time.perf_counter() - t0, 2)
+        out["device_build_same_k"] = pd.info["k"] == info["k"]
+        pd.close()
+    return out
 
 
 def load_peaks():

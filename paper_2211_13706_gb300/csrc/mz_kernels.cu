@@ -667,9 +667,9 @@ __device__ __forceinline__ void pace_until(int64_t ns) {
 template <class M, int NV, bool SUB>
 __device__ __forceinline__ void sum_in_order(unsigned long long *v, const int32_t *id, const unsigned long long *P,
                                              const unsigned char *E, typename M::T &acc, uint32_t *status,
-                                             int64_t limit) {
+                                             int64_t limit, int start) {
     const unsigned long long S = M::kSentinel;
-    int next = 0;
+    int next = start;   // words before `start` are the row's padding (slot 0, the value 0)
     auto advance = [&]() {
 #pragma unroll
         for (int j = 0; j < NV; ++j)
@@ -764,6 +764,13 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
             unsigned long long vprev = ANTI ? ld_relaxed_u64(Pb + (sout - 1) * B) : 0ull;
             int32_t id[kChunk], nid[kChunk];
             load_ids(row, id, a.nslots, a.status);
+            // The row's padding: slot 0 (a zero slot, never an element) in front of its entries.
+            // Its words are 0, and subtracting or adding them (from g(x), or from a sum that
+            // starts at +0) leaves every bit as it is, so they are skipped: fp64 adds are what
+            // bounds this kernel on GB300, and rows of posets with few chains are mostly padding.
+            int lead = 0;
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) lead += id[j] == 0;
             // U form: acc runs as g(x) - (sum of the values so far), so that once the last
             // value lands one subtraction is left; the antichain form sums, as it needs
             // y'(next(x)) apart.
@@ -772,12 +779,13 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
             for (int c0 = 0; c0 + kChunk < kp; c0 += kChunk) {
                 unsigned long long v[kChunk];
                 int32_t sid[kChunk];
+                const int start = c0 == 0 ? lead : 0;
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) sid[j] = (int32_t)((int64_t)id[j] * B);
 #pragma unroll
-                for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(Pb + sid[j]);
+                for (int j = 0; j < kChunk; ++j) v[j] = j < start ? 0ull : ld_relaxed_u64(Pb + sid[j]);
                 load_ids(row + c0 + kChunk, nid, a.nslots, a.status);
-                sum_in_order<M, kChunk, !ANTI>(v, sid, Pb, Eb, acc, a.status, a.spin_limit);
+                sum_in_order<M, kChunk, !ANTI>(v, sid, Pb, Eb, acc, a.status, a.spin_limit, start);
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) id[j] = nid[j];
             }
@@ -788,11 +796,12 @@ __global__ void __launch_bounds__(128) k_mob_wave_t(MobArgs a) {
                 const unsigned long long S = SENT;
                 unsigned long long v[kChunk];
                 int64_t sid[kChunk];
+                const int start = kp == kChunk ? lead : 0;   // the row's only chunk holds its padding
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j) sid[j] = (int64_t)id[j] * B;
 #pragma unroll
-                for (int j = 0; j < kChunk; ++j) v[j] = ld_relaxed_u64(Pb + sid[j]);
-                int next = 0;
+                for (int j = 0; j < kChunk; ++j) v[j] = j < start ? 0ull : ld_relaxed_u64(Pb + sid[j]);
+                int next = start;
                 for (int64_t it = 0;; ++it) {
 #pragma unroll
                     for (int j = 0; j < kChunk; ++j)
