@@ -84,6 +84,8 @@ CASES = {
                          kw=dict(device_build=1, build_transpose=1)),
     "device_build_sparse": dict(poset=lambda: pg.planted_chain_poset(2000, 40, 6, cross_deg=2),
                                 kw=dict(device_build=1, niv_format=2)),
+    # chains by Alg. 1's matching on the device (the ER DAG comes without chains)
+    "device_build_matching": dict(poset=lambda: pg.er_dag(3000, 3, 7), kw=dict(device_build=2)),
 }
 
 
