@@ -35,8 +35,15 @@
  *  - f, g and ws are device pointers the caller owns. Input and output must
  *    not overlap. Calls on one workspace must not overlap in time.
  *  - Errors found on the host are returned directly and nothing is launched.
- *    Errors found on the device (a bounded wait that ran out) are recorded in
- *    the plan and returned by mz_check. Outputs are undefined after an error.
+ *    Errors found on the device (a bounded wait that ran out; in the MZ_DEBUG
+ *    build also an index outside its array) are recorded in the plan and
+ *    returned by mz_check. Outputs are undefined after an error.
+ *
+ * Debug build: the same sources compiled with MZ_DEBUG (libmz_debug.so) check
+ * every index a transform kernel takes from the niv map or a plan table before
+ * using it (MZ_ERR_BOUNDS through mz_check, the access skipped, never a trap)
+ * and fill the workspace and the output with a poison pattern (all bytes 0xFF)
+ * before each transform, so that a word left unwritten shows in the result.
  */
 #ifndef MZ_H
 #define MZ_H
@@ -280,7 +287,8 @@ mz_status mz_mobius_T(const mz_plan *plan, mz_dtype dtype, const void *h, void *
 /*
  * mz_check - synchronises `stream`, then returns and clears the plan's device-side
  * status word, which every transform of the plan sets when one of its bounded waits
- * runs out (MZ_OK or MZ_ERR_TIMEOUT; the word is shared by all calls of the plan).
+ * runs out (MZ_OK or MZ_ERR_TIMEOUT, and MZ_ERR_BOUNDS in the MZ_DEBUG build; the word
+ * is shared by all calls of the plan).
  * MZ_ERR_CUDA if the stream reports an error.
  */
 mz_status mz_check(const mz_plan *plan, mz_stream stream);
