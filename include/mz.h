@@ -319,6 +319,29 @@ mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info);
    entries offset to the union); their niv map is not exported (MZ_ERR_UNSUPPORTED). */
 mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *out, size_t bytes);
 
+/*
+ * mz_plan_save - writes the plan's one-time precomputation (for every poset and the
+ * dual: order, chains, slot layout, niv map, heights and U levels) to the file `path`,
+ * so that mz_plan_load can rebuild the plan without computing it again. The format
+ * is this library's (magic, version, checksum; the byte order and type sizes of the
+ * writing machine). A plan whose niv map was built with device_build keeps the map
+ * only on the device: MZ_ERR_UNSUPPORTED (build it with device_build = 0 to save it).
+ * MZ_ERR_INVALID_ARG if the file cannot be written.
+ */
+mz_status mz_plan_save(const mz_plan *plan, const char *path);
+
+/*
+ * mz_plan_load - a plan from a file written by mz_plan_save. From `opts` (NULL: the
+ * defaults) it takes what concerns the device part: host_only, mobius_schedule,
+ * mobius_blocks_per_sm, mobius_pace_ns, spin_limit, debug_withhold and the allocator
+ * callbacks; build_transpose, niv_format and device_build are the saved plan's. The
+ * file is checked before anything is uploaded (magic, version, checksum, every array
+ * length and every index against its range): MZ_ERR_INVALID_ARG names what failed, and
+ * no file can make a kernel read outside an array. MZ_ERR_OOM, MZ_ERR_CUDA as mz_build;
+ * *out is NULL on any error.
+ */
+mz_status mz_plan_load(const char *path, const mz_build_opts *opts, mz_plan **out);
+
 /* Kernel launches issued by the last transform call on this thread (memsets excluded). */
 int32_t mz_last_launch_count(void);
 

@@ -35,8 +35,8 @@ MZ_EXPORT_CHAIN_ID, MZ_EXPORT_CHAIN_POS, MZ_EXPORT_NIV, MZ_EXPORT_LEVEL, MZ_EXPO
 # every symbol include/mz.h declares
 EXPORTED = ["mz_build", "mz_build_batch", "mz_destroy", "mz_workspace_size", "mz_zeta", "mz_zeta_noalloc", "mz_mobius",
             "mz_zeta_T", "mz_mobius_T",
-            "mz_check", "mz_plan_tune", "mz_plan_info", "mz_plan_export", "mz_last_launch_count", "mz_set_launch_events",
-            "mz_status_string", "mz_last_error"]
+            "mz_check", "mz_plan_tune", "mz_plan_info", "mz_plan_export", "mz_plan_save", "mz_plan_load",
+            "mz_last_launch_count", "mz_set_launch_events", "mz_status_string", "mz_last_error"]
 
 
 class MzError(RuntimeError):
@@ -150,6 +150,8 @@ def _load():
     lib.mz_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     lib.mz_plan_tune.argtypes = [vp, ctypes.POINTER(Tuning), ctypes.POINTER(Tuning)]
     lib.mz_plan_export.argtypes = [vp, i32, i32, vp, sz]
+    lib.mz_plan_save.argtypes = [vp, ctypes.c_char_p]
+    lib.mz_plan_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
     lib.mz_last_launch_count.argtypes = []
     lib.mz_last_launch_count.restype = i32
     lib.mz_set_launch_events.argtypes = [vp, i32]
@@ -305,6 +307,25 @@ def mz_plan_export(plan: int, what: int, dual: bool = False) -> np.ndarray:
     return out.reshape(info["n"], info["k"]) if what == MZ_EXPORT_NIV else out
 
 
+def mz_plan_save(plan: int, path: str) -> None:
+    """mz_plan_save: the plan's precomputation to a file."""
+    _check(lib.mz_plan_save(plan, os.fsencode(path)), "mz_plan_save")
+
+
+def mz_plan_load(path: str, *, host_only: bool = False, mobius_schedule: int = MZ_SCHED_ULEVEL,
+                 spin_limit: int = 0, debug_withhold: int = 0, mobius_blocks_per_sm: int = 0,
+                 mobius_pace_ns: int = 0, torch_allocator: bool = False) -> int:
+    """mz_plan_load: a plan handle from a file written by mz_plan_save."""
+    opts = _opts(False, host_only, mobius_schedule, mobius_blocks_per_sm, mobius_pace_ns, 0,
+                 spin_limit, debug_withhold, 0, torch_allocator)
+    out = ctypes.c_void_p()
+    st = lib.mz_plan_load(os.fsencode(path), ctypes.byref(opts), ctypes.byref(out))
+    if st != MZ_OK:
+        _check_alloc_errors()
+    _check(st, "mz_plan_load")
+    return out.value
+
+
 def mz_last_launch_count() -> int:
     return int(lib.mz_last_launch_count())
 
@@ -350,6 +371,15 @@ class Plan:
         """One plan for many posets: a list of (n, src, dst, chain_id or None). Values are
         [sum n] or [sum n, batch] arrays, poset after poset."""
         return cls(0, None, None, _handle=mz_build_batch(posets, **opts))
+
+    @classmethod
+    def load(cls, path, **opts):
+        """A plan from a file written by Plan.save (mz_plan_load); opts as mz_plan_load."""
+        return cls(0, None, None, _handle=mz_plan_load(path, **opts))
+
+    def save(self, path):
+        """Writes the plan's precomputation to `path` (mz_plan_save)."""
+        mz_plan_save(self.handle, path)
 
     def close(self):
         if getattr(self, "handle", None):

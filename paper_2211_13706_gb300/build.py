@@ -1,6 +1,6 @@
 """Builds libmz.so (the C ABI of include/mz.h) in-tree for sm_103a.
 
-Four translation units compiled in parallel, then linked with the CUDA
+Five translation units compiled in parallel, then linked with the CUDA
 runtime statically. Output: paper_2211_13706_gb300/_build/libmz.so.
 
 The debug variant, libmz_debug.so, is the same sources compiled with MZ_DEBUG:
@@ -23,7 +23,7 @@ LIB = os.path.join(OUT, "libmz.so")
 LIB_DEBUG = os.path.join(OUT, "libmz_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["mz_host.cpp", "mz_kernels.cu", "mz_build.cu", "mz_abi.cu"]
+SOURCES = ["mz_host.cpp", "mz_plan_io.cpp", "mz_kernels.cu", "mz_build.cu", "mz_abi.cu"]
 
 
 def _nvcc() -> str:

@@ -1390,6 +1390,8 @@ static mz_status build_components(mz_plan *p, int32_t count, const int64_t *n, c
     return MZ_OK;
 }
 
+static mz_status finish_plan(std::unique_ptr<mz_plan> &p, const mz_build_opts &o, mz_plan **out);
+
 static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, const int32_t *const *src,
                             const int32_t *const *dst, const int32_t *const *chain_id, const mz_build_opts *opts,
                             mz_plan **out) {
@@ -1451,6 +1453,13 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
                     set_last_error("device_build of several posets needs dense niv maps (k <= 512 chains each)");
                     return MZ_ERR_UNSUPPORTED;
                 }
+    return finish_plan(p, o, out);
+}
+
+// The device part of a plan whose host sides are complete (a build or a plan file): the
+// settings of the options, then the upload of every side; *out gets the plan.
+static mz_status finish_plan(std::unique_ptr<mz_plan> &p, const mz_build_opts &o, mz_plan **out) {
+    mz_status st = MZ_OK;
     p->schedule = o.mobius_schedule;
     p->host_only = o.host_only != 0;
     if (o.spin_limit > 0) p->spin_limit = o.spin_limit;
@@ -1718,6 +1727,57 @@ mz_status mz_plan_info(const mz_plan *plan, mz_plan_info_t *info) {
         info->wave_entries = plan->dev[0].nmob_entries;
     }
     return MZ_OK;
+}
+
+mz_status mz_plan_save(const mz_plan *plan, const char *path) {
+    if (!plan || !path) {
+        set_last_error("null plan or path");
+        return MZ_ERR_INVALID_ARG;
+    }
+    for (int side = 0; side < (plan->has_dual ? 2 : 1); ++side)
+        for (const HostSide &H : plan->host[side])
+            if (H.niv_on_device) {
+                set_last_error("the niv map of a plan built with device_build exists only on the device; "
+                               "a plan built with device_build = 0 can be saved");
+                return MZ_ERR_UNSUPPORTED;
+            }
+    std::string err;
+    const mz_status st = save_host_sides(plan, path, err);
+    if (st) set_last_error(err);
+    return st;
+}
+
+mz_status mz_plan_load(const char *path, const mz_build_opts *opts, mz_plan **out) {
+    if (out) *out = nullptr;
+    if (!path || !out) {
+        set_last_error("null path or out");
+        return MZ_ERR_INVALID_ARG;
+    }
+    mz_build_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr)) {
+        set_last_error("dev_alloc and dev_free must be given together");
+        return MZ_ERR_INVALID_ARG;
+    }
+    if (o.mobius_schedule != MZ_SCHED_ULEVEL && o.mobius_schedule != MZ_SCHED_ANTICHAIN) {
+        set_last_error("unknown mobius_schedule");
+        return MZ_ERR_INVALID_ARG;
+    }
+    std::unique_ptr<mz_plan> p;
+    try {
+        p.reset(new mz_plan());
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return MZ_ERR_OOM;
+    }
+    std::string err;
+    const mz_status st = load_host_sides(p.get(), path, err);
+    if (st) {
+        set_last_error(err);
+        return st;
+    }
+    return finish_plan(p, o, out);
 }
 
 mz_status mz_plan_export(const mz_plan *plan, int32_t what, int32_t dual, void *out, size_t bytes) {

@@ -147,6 +147,12 @@ mz_status build_host_side(int64_t n, const std::vector<int32_t> &src, const std:
 
 void set_last_error(const std::string &s);
 
+// Plan files (mz_plan_io.cpp): the host sides of every poset (the dual included) and the
+// plan's flags. load_host_sides fills p->host, p->has_dual and the offsets of the union,
+// after checking every length and index; the device part is built from them afterwards.
+mz_status save_host_sides(const mz_plan *p, const char *path, std::string &err);
+mz_status load_host_sides(mz_plan *p, const char *path, std::string &err);
+
 // Caps the host threads build_host_side uses on the calling thread (0: no cap); set to 1
 // where several posets are built at once, one per thread.
 void set_host_threads_cap(int cap);
