@@ -119,6 +119,48 @@ def test_damaged_and_crafted_files_are_refused(tmp_path):
     mz.Plan.load(str(good), host_only=True)
 
 
+@pytest.mark.parametrize("kind", ["dense", "sparse"])
+def test_mutated_files_never_load_out_of_range(tmp_path, kind):
+    """Random 4-byte words of a valid file overwritten with random values (small, negative,
+    huge), checksum recomputed: the loader either refuses the file with MZ_ERR_INVALID_ARG
+    or gives a plan whose exports stay in range; it never crashes."""
+    if kind == "dense":
+        p = pg.planted_chain_poset(300, 5, 8, cross_deg=2)
+        plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, host_only=True, build_transpose=True)
+    else:
+        p = pg.er_dag(300, 3, 8)
+        plan = mz.Plan(p.n, p.src, p.dst, None, host_only=True, niv_format=2)
+    good = tmp_path / "good.mzplan"
+    plan.save(str(good))
+    body = good.read_bytes()[:-8]
+    rng = np.random.default_rng(11)
+    bad = tmp_path / "bad.mzplan"
+    loaded = refused = 0
+    for _ in range(300):
+        m = bytearray(body)
+        for _ in range(int(rng.integers(1, 4))):
+            off = int(rng.integers(24, len(m) - 4)) & ~3
+            val = int(rng.choice([rng.integers(-3, 3), rng.integers(0, 2 * p.n), rng.integers(-2**31, 2**31)]))
+            struct.pack_into("<i", m, off, val)
+        bad.write_bytes(_reseal(bytes(m)))
+        try:
+            q = mz.Plan.load(str(bad), host_only=True)
+        except mz.MzError as e:
+            assert e.status == mz.MZ_ERR_INVALID_ARG, str(e)
+            refused += 1
+            continue
+        loaded += 1
+        n, k = q.info["n"], q.info["k"]
+        cid = q.export(mz.MZ_EXPORT_CHAIN_ID)
+        assert ((cid >= 0) & (cid < k)).all()
+        topo = q.export(mz.MZ_EXPORT_TOPO)
+        assert np.array_equal(np.sort(topo), np.arange(n))
+        niv = q.export(mz.MZ_EXPORT_NIV)
+        assert ((niv >= -1) & (niv < n)).all()
+        q.close()
+    assert refused > 0
+
+
 def test_save_and_load_arguments(tmp_path):
     p = pg.paper_example()
     plan = mz.Plan(p.n, p.src, p.dst, None, host_only=True)
