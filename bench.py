@@ -117,6 +117,27 @@ def time_single(mz, torch, wl: str, dtype_key: str, steps: int = 10, seed: int =
     return out
 
 
+def time_plan_file(mz, plan, info):
+    """The plan's precomputation written to a file and loaded back into a device plan
+    (mz_plan_save / mz_plan_load): sizes and wall times; outside every timed region."""
+    import tempfile
+    try:
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "plan.mzplan")
+            t0 = time.perf_counter()
+            plan.save(path)
+            save_s = time.perf_counter() - t0
+            size = os.path.getsize(path)
+            t0 = time.perf_counter()
+            loaded = mz.Plan.load(path)
+            load_s = time.perf_counter() - t0
+            same = loaded.info == info
+            loaded.close()
+        return {"bytes": size, "save_s": round(save_s, 3), "load_s": round(load_s, 3), "same_plan_info": bool(same)}
+    except Exception as exc:          # keep the measured line; say what failed
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -905,6 +926,7 @@ def device_arm(args):
                 np.array_equal(pd.export(mz.MZ_EXPORT_ULEVEL), plan.export(mz.MZ_EXPORT_ULEVEL))
             variants["plan_build"] = {"host_s": round(build_s, 3), "device_s": round(dev_s, 3), "same_plan": bool(same)}
             pd.close()
+        variants["plan_file"] = time_plan_file(mz, plan, info)
         pa = mz.Plan(p.n, p.src, p.dst, p.chain_id, mobius_schedule=mz.MZ_SCHED_ANTICHAIN)
         kta, tot, _, _, _, _ = time_transforms(mz, pa, x, 3, 1, torch, flush, anti=True)
         variants["mobius_antichain_schedule_" + args.dtype] = {

@@ -70,3 +70,17 @@ def test_accuracy_leg_measures_errors():
     bad_g[rows[0]] *= 1 + 1e-6
     e = bench.oracle_row_errors(p, {"f64": (f, bad_g, m)}, [int(rows[0])])
     assert 1e-8 < e["f64"]["zeta_max_rel"] < 1e-5
+
+
+def test_plan_file_leg(monkeypatch):
+    """The plan-file variant: a host-only plan saved, loaded back (the loader is pointed at
+    host-only loads, as there is no device here), sizes and times reported; a failure
+    becomes an error entry instead of ending the bench line."""
+    p = pg.planted_chain_poset(2000, 8, 4, cross_deg=2)
+    plan = mz.Plan(p.n, p.src, p.dst, p.chain_id, host_only=True)
+    real_load = mz.Plan.load
+    monkeypatch.setattr(mz.Plan, "load", classmethod(lambda cls, path, **kw: real_load(path, host_only=True)))
+    out = bench.time_plan_file(mz, plan, plan.info)
+    assert out["same_plan_info"] and out["bytes"] > 4 * p.n * 8 and out["load_s"] >= 0
+    monkeypatch.setattr(mz.Plan, "load", classmethod(lambda cls, path, **kw: (_ for _ in ()).throw(OSError("x"))))
+    assert "error" in bench.time_plan_file(mz, plan, plan.info)
