@@ -14,6 +14,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>   // header-only; the ranges cost nothing unless a profiler is attached
+
 #include "mz_internal.h"
 #include "mz_kernels.h"
 
@@ -37,6 +39,15 @@ static mz_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// An NVTX range over a scope: the build's phases and every transform call show up by
+// name on a profiler's host timeline (Nsight Systems, ncu --nvtx).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---------------------------------------------------------------- device memory of a plan
 static void *plan_alloc(mz_plan *p, size_t bytes) {
@@ -1222,6 +1233,7 @@ static mz_status debug_poison(const mz_plan *p, int side, void *ws, size_t ws_by
 
 static mz_status run_zeta(const mz_plan *p, int side, mz_dtype dtype, const void *f, void *g, int32_t B, void *ws,
                           size_t ws_bytes, mz_stream stream) {
+    NvtxRange range(side ? "mz_zeta_T" : "mz_zeta");
     g_last_launches = 0;
     WsLayout L;
     mz_status st = check_call(p, dtype, f, g, B, ws, ws_bytes, side, &L);
@@ -1272,6 +1284,7 @@ static mz_status run_zeta(const mz_plan *p, int side, mz_dtype dtype, const void
 
 static mz_status run_mobius(const mz_plan *p, int side, mz_dtype dtype, const void *g, void *f, int32_t B, void *ws,
                             size_t ws_bytes, mz_stream stream) {
+    NvtxRange range(side ? "mz_mobius_T" : "mz_mobius");
     g_last_launches = 0;
     WsLayout L;
     mz_status st = check_call(p, dtype, g, f, B, ws, ws_bytes, side, &L);
@@ -1443,8 +1456,12 @@ static mz_status build_plan(int32_t count, const int64_t *n, const int64_t *m, c
         set_last_error("device_build is 0, 1 or 2");
         return MZ_ERR_INVALID_ARG;
     }
-    mz_status st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0, o.niv_format,
-                                    o.device_build != 0, o.device_build == 2);
+    mz_status st;
+    {
+        NvtxRange range("mz_build: host sides (order, chains, slots, levels)");
+        st = build_components(p.get(), count, n, m, src, dst, chain_id, o.build_transpose != 0, o.niv_format,
+                              o.device_build != 0, o.device_build == 2);
+    }
     if (st) return st;
     if (o.device_build && count > 1)
         for (int side = 0; side < (p->has_dual ? 2 : 1); ++side)
@@ -1481,6 +1498,7 @@ static mz_status finish_plan(std::unique_ptr<mz_plan> &p, const mz_build_opts &o
         } else if ((e = cudaMemset(p->d_status, 0, 256)) != cudaSuccess) {
             st = cuda_fail(e, "cudaMemset");
         }
+        NvtxRange range("mz_build: device part (uploads, device build)");
         for (int side = 0; side < (p->has_dual ? 2 : 1) && st == MZ_OK; ++side)
             st = !p->host[side][0].niv_on_device ? upload_side(p.get(), side)
                  : p->components() > 1            ? upload_batch_device(p.get(), side)
@@ -1741,6 +1759,7 @@ mz_status mz_plan_save(const mz_plan *plan, const char *path) {
                                "a plan built with device_build = 0 can be saved");
                 return MZ_ERR_UNSUPPORTED;
             }
+    NvtxRange range("mz_plan_save");
     std::string err;
     const mz_status st = save_host_sides(plan, path, err);
     if (st) set_last_error(err);
@@ -1771,6 +1790,7 @@ mz_status mz_plan_load(const char *path, const mz_build_opts *opts, mz_plan **ou
         set_last_error("host allocation failed");
         return MZ_ERR_OOM;
     }
+    NvtxRange range("mz_plan_load");
     std::string err;
     const mz_status st = load_host_sides(p.get(), path, err);
     if (st) {
